@@ -1,0 +1,269 @@
+/*
+ * sr.h -- C ABI of the B300 short-range particle-particle force library.
+ *
+ * The library evaluates the short-range half of a split long/short-range
+ * gravity solver (the paper's Sec. 2: a spectrally filtered PM long-range
+ * force plus direct particle-particle sums inside a cutoff r_c), with the
+ * on-node work decomposition of Sec. 2.1 (partition into overlapping blocks
+ * with active and passive particles, evolve, reconcile) and the kick that
+ * ends the step.  Force law (unit masses, G = 1, periodic box of side L):
+ *
+ *   a_i = sum_{j != i, |d_ij| < r_c} d_ij f_SR(|d_ij|^2),   d_ij = x_j - x_i (minimum image)
+ *   f_SR(s) = (s + eps^2)^(-3/2) - p(s),
+ *
+ * p a degree-5 polynomial least-squares fit of the Gaussian-split long-range
+ * force F_long(r)/r, F_long(r) = (1/r^2)[erf(r/2 sigma) - (r/(sigma sqrt pi)) exp(-r^2/4 sigma^2)].
+ *
+ * Conventions for every entry point:
+ *  - Return value: SR_OK (0) or an SR_ERR_* code; the message of the last
+ *    failure on the calling thread is returned by sr_last_error().  Nothing
+ *    is thrown across the ABI.
+ *  - "device" pointers are CUDA global-memory pointers on the current
+ *    device; "host" pointers are CPU memory.  The caller owns every buffer it
+ *    passes; the plan owns its workspace.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Entry points that take a stream only enqueue work: they do not
+ *    allocate, free or synchronise, so they can be captured into a CUDA
+ *    graph (sr_force_plain is the exception, see there).
+ *  - Positions are binary64 arrays of N rows (x, y, z), row-major (AoS).
+ *    Velocities, accelerations and their cotangents are binary32 arrays of
+ *    N rows (x, y, z, w) (16-byte float4 rows; w is ignored on input and
+ *    written as 0 on output).  Rows follow the caller's particle order; for a
+ *    batch plan, volumes are concatenated in plan order.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SR_OK            0
+#define SR_ERR_ARG       1   /* invalid argument (null pointer, bad size or parameter) */
+#define SR_ERR_CUDA      2   /* a CUDA runtime call failed (message has the CUDA error) */
+#define SR_ERR_CAPACITY  3   /* n exceeds the plan's capacity */
+#define SR_ERR_STATE     4   /* call order violated (e.g. sr_force before sr_bin) */
+#define SR_ERR_RANGE     5   /* a position was non-finite or outside [-L, 2L) */
+
+/* Polynomial fit modes. */
+#define SR_FIT_CONSTRAINED    0  /* least squares with p(r_c^2) = (r_c^2+eps^2)^(-3/2): f_SR(r_c^2) = 0 */
+#define SR_FIT_UNCONSTRAINED  1  /* plain least squares */
+
+/* Export selectors for sr_plan_copy (all refer to the last sr_bin). */
+#define SR_EXPORT_PERM              0  /* int32[n]: sorted position -> caller index */
+#define SR_EXPORT_CELL_START        1  /* int32[total_cells+1]: first sorted position of each cell */
+#define SR_EXPORT_CELL_CHUNK_START  2  /* int32[total_cells+1]: first chunk of each cell */
+#define SR_EXPORT_SLOT_POS          3  /* float[4*32*n_chunks]: chunk-relative offsets (units of h) */
+#define SR_EXPORT_SLOT_IDX          4  /* int32[32*n_chunks]: caller index per slot, -1 = empty */
+#define SR_EXPORT_CHUNK_META        5  /* int32[4*n_chunks]: anchor (qx, qy, qz) and volume */
+#define SR_EXPORT_CHUNK_LO          6  /* float[4*n_chunks]: bbox min (x,y,z), w = particle count (int bits) */
+#define SR_EXPORT_CHUNK_HI          7  /* float[4*n_chunks]: bbox max (x,y,z), w = 0 */
+#define SR_EXPORT_ORDER             8  /* int32[n_chunks]: work order of the persistent kernel */
+#define SR_EXPORT_COST              9  /* uint32[n_chunks]: estimated pair evaluations per chunk */
+#define SR_EXPORT_COUNTERS         10  /* int64[8]: n_chunks, queue head, error bits, ... */
+
+/* Physics and binning parameters of one periodic volume (lengths in the
+ * same unit as the positions; the workloads use the mean inter-particle
+ * spacing). */
+typedef struct sr_params {
+    double box;       /* L > 2 r_c: periodic box side                                  */
+    double r_c;       /* cutoff radius (> 0)                                           */
+    double eps;       /* Plummer softening (> 0)                                       */
+    double sigma;     /* Gaussian split scale (> 0)                                    */
+    int    fit_mode;  /* SR_FIT_CONSTRAINED or SR_FIT_UNCONSTRAINED                    */
+    int    n_cells;   /* cells per axis; 0 = automatic (side close to 4, >= r_c)        */
+    int    sub_bits;  /* Morton bits per axis inside a cell (1..8); 0 = automatic (6)  */
+    int    reserved;  /* must be 0                                                     */
+} sr_params;
+
+/* Read-only description of a plan (sizes of the exportable arrays). */
+typedef struct sr_plan_info {
+    int64_t n_particles;   /* particles of the last sr_bin (capacity before the first)  */
+    int64_t capacity;      /* maximum particles                                        */
+    int64_t n_volumes;
+    int64_t total_cells;   /* sum over volumes of n_cells^3                            */
+    int64_t max_chunks;    /* capacity of the chunk arrays                             */
+    int64_t n_chunks;      /* chunks of the last sr_bin (reads device memory; syncs)   */
+    int32_t sub_bits;
+    int32_t key_bits;      /* significant bits of the sort key                         */
+    int32_t workers;       /* resident warps of the persistent force kernel            */
+    int32_t warps_per_block;
+    double  coef[6];       /* fitted p(s) = sum_k coef[k] s^k (binary64)               */
+} sr_plan_info;
+
+typedef struct sr_plan sr_plan;
+
+/*
+ * sr_fit_poly -- fit p(s) = sum_k c_out[k] s^k to F_long(sqrt s)/sqrt s on
+ * [0, r_c^2] (host only; no GPU needed).  Reading of the fit (the paper,
+ * Sec. 2, names the filtered split but prints no polynomial): 4096 midpoint
+ * samples s_k = r_c^2 (k + 1/2)/4096, unweighted least squares in the basis
+ * (s/r_c^2)^m solved by Householder QR in binary64; mode CONSTRAINED also
+ * imposes p(r_c^2) = (r_c^2 + eps^2)^(-3/2).
+ * c_out: host array of 6 doubles, written on success.
+ * Errors: SR_ERR_ARG for non-positive r_c or sigma, negative eps, bad mode
+ * or null c_out.
+ */
+int sr_fit_poly(double r_c, double sigma, double eps, int mode, double c_out[6]);
+
+/*
+ * sr_plan_create -- plan for one periodic volume holding at most n_max
+ * particles.  Allocates all device workspace (about 100 bytes per particle
+ * plus 8 bytes per cell) on the current device; no later call allocates.
+ * Binning (Sec. 2.1 step 1, "partition into overlapping blocks"): cells of
+ * side L/n_cells >= r_c; each cell's particles in Morton order of their
+ * sub-cell (2^sub_bits per axis); chunks of <= 32 consecutive particles per
+ * cell are the work units, each with a binary64 anchor and binary32 offsets.
+ * Errors: SR_ERR_ARG (bad parameters, n_max < 1 or > 2^30), SR_ERR_CUDA
+ * (allocation failed).  *out is NULL on failure.
+ */
+int sr_plan_create(const sr_params* params, int64_t n_max, sr_plan** out);
+
+/*
+ * sr_plan_batch -- plan for n_vol independent periodic volumes evaluated
+ * together (one binning, one persistent force launch).  params[v].box and
+ * n_cells may differ per volume; r_c, eps, sigma, fit_mode and sub_bits
+ * must be equal.  n[v] (host array) is volume v's particle count; sr_bin
+ * then takes the concatenation, sum n[v] rows.
+ * Errors: as sr_plan_create, plus SR_ERR_ARG for mismatched physics.
+ */
+int sr_plan_batch(const sr_params* params, const int64_t* n, int n_vol, sr_plan** out);
+
+/* sr_plan_destroy -- free a plan and its workspace (synchronises the device). */
+int sr_plan_destroy(sr_plan* plan);
+
+/* sr_plan_get_info -- fill *info (host). Synchronises to read n_chunks. */
+int sr_plan_get_info(sr_plan* plan, sr_plan_info* info);
+
+/*
+ * sr_plan_volume_info -- geometry of volume v (host outputs, each nullable):
+ * its particle count (capacity for a single-volume plan), box side, cells
+ * per axis, and fine-grid side h = L / (n_cells 2^sub_bits).
+ * Errors: SR_ERR_ARG for a null plan or v out of range.
+ */
+int sr_plan_volume_info(const sr_plan* plan, int v, int64_t* n, double* box, int* n_cells,
+                        double* h);
+
+/*
+ * sr_bin -- bit-exact cell binning and stable counting sort (Sec. 2.1
+ * step 1).  pos: device, n rows of binary64 (x, y, z).  Positions in
+ * [-L, 2L) are folded into [0, L) (x<0: x+L, then x>=L: x-L); the fine
+ * grid is h = L/(n_cells 2^sub_bits), q = min(floor(x/h), M-1); sort key
+ * (cell << 3 sub_bits) | morton(sub-cell), ties by caller index; chunk
+ * offsets binary32(x/h - qA).  Also computes each chunk's cost estimate and
+ * the longest-first work order for sr_force.
+ * Errors: SR_ERR_ARG (null pos), SR_ERR_CAPACITY (n > capacity; for a batch
+ * plan n must equal the sum of n[v]).  Out-of-range or non-finite
+ * positions do not fail the call: they are binned as 0 and flagged, and
+ * sr_plan_status then returns SR_ERR_RANGE.
+ */
+int sr_bin(sr_plan* plan, const double* pos, int64_t n, void* stream);
+
+/*
+ * sr_force -- short-range accelerations of every binned particle (Sec. 2,
+ * direct particle-particle sums; Sec. 2.1 steps 2-3: each chunk is an
+ * active block reading its passive neighbours within r_c, and only active
+ * particles are written).  One persistent launch: each warp repeatedly takes
+ * the next chunk from the longest-first order, culls neighbour chunks and
+ * particles by bounding boxes, stages the survivors through shared memory
+ * and accumulates per-32-neighbour binary32 partial sums into a Kahan
+ * (compensated) sum.  No float atomics: results are run-to-run identical.
+ * acc: device, n rows float4 (written, caller order).
+ * pair_count: device uint64, nullable: if given, the kernel also counts the
+ *   ordered in-range pairs (i != j) under the binary32 predicate
+ *   s' = fma(dz,dz,fma(dy,dy,fma(dx,dx,eps^2/h^2))) < (r_c^2+eps^2)/h^2
+ *   and ADDS the total to *pair_count.
+ * per_particle: device int32[n], nullable: per-particle in-range counts
+ *   (written, caller order); counting mode runs a slower kernel variant.
+ * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null acc).
+ */
+int sr_force(sr_plan* plan, float* acc, unsigned long long* pair_count,
+             int* per_particle, void* stream);
+
+/*
+ * sr_force_plain -- the same accelerations from the plain kernel: one
+ * launch per z-slab of cells, one thread per particle slot, neighbour
+ * particles read straight from global memory over the 27 neighbour cells,
+ * no culling and no work queue.  It is the reference point for the
+ * persistent kernel's speed-up.  Unlike the other calls it copies the
+ * cell-to-chunk table to the host (one synchronisation) to size its
+ * launches, so it cannot be captured into a CUDA graph.
+ */
+int sr_force_plain(sr_plan* plan, float* acc, void* stream);
+
+/*
+ * sr_force_vjp -- vector-Jacobian product of the accelerations with respect
+ * to the positions, gather form (no atomics):
+ *   xbar_i (+)= g_scale * sum_j [ f(s)(g_j - g_i) + 2 f'(s) (d.(g_j - g_i)) d ],
+ *   d = x_j - x_i, f'(s) = -3/2 (s+eps^2)^(-5/2) - p'(s),
+ * for the positions of the last sr_bin.  g_acc: device float4 rows (the
+ * cotangent on acc); g_pos: device float4 rows, overwritten (accumulate = 0)
+ * or added to (accumulate = 1).
+ * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null pointers).
+ */
+int sr_force_vjp(sr_plan* plan, const float* g_acc, float* g_pos, float g_scale,
+                 int accumulate, void* stream);
+
+/*
+ * sr_kick -- v += a * dt for n float4 rows (x, y, z; w untouched).
+ * acc, vel: device.  Errors: SR_ERR_ARG (null pointers, n < 0).
+ */
+int sr_kick(int64_t n, const float* acc, float* vel, float dt, void* stream);
+
+/*
+ * sr_drift -- x <- fold(x + v dt) in binary64 for the plan's volumes
+ * (x + double(v) * dt, then x<0: x+L, x>=L: x-L).  pos: device binary64
+ * rows (x, y, z), updated in place; vel: device float4 rows; n as for
+ * sr_bin.  Errors: SR_ERR_ARG, SR_ERR_CAPACITY.
+ */
+int sr_drift(sr_plan* plan, double* pos, const float* vel, double dt, int64_t n, void* stream);
+
+/*
+ * sr_invariants -- binary64 global sums of n float4 rows, in a fixed
+ * reduction order (deterministic): out[0..2] = sum v, out[3..5] = sum a,
+ * out[6] = sum |v|^2 / 2 (unit masses).  vel, acc: device; out: device
+ * double[7], overwritten.  Either input may be NULL (its sums are 0).  The
+ * plan provides the reduction workspace; n must not exceed its capacity.
+ */
+int sr_invariants(sr_plan* plan, int64_t n, const float* vel, const float* acc, double* out,
+                  void* stream);
+
+/*
+ * sr_plan_status -- synchronise the stream and report device-side flags of
+ * the last calls: SR_ERR_RANGE if sr_bin saw a non-finite or out-of-range
+ * position (the flag is then cleared), else SR_OK.
+ */
+int sr_plan_status(sr_plan* plan, void* stream);
+
+/*
+ * sr_plan_copy -- copy one internal array of the last sr_bin (selector
+ * SR_EXPORT_*) into dst (device or host memory, cudaMemcpyDefault), at most
+ * bytes bytes, on stream.  For inspection and tests.
+ */
+int sr_plan_copy(sr_plan* plan, int which, void* dst, int64_t bytes, void* stream);
+
+/*
+ * sr_step_host -- one whole step from host buffers (end-to-end form): copy
+ * pos (host binary64 rows) and vel (host float4 rows) to plan-owned device
+ * buffers, sr_bin, sr_force, sr_kick, copy acc (host float4 rows, nullable)
+ * and the updated vel back, and wait for completion.  Host buffers should be
+ * page-locked for overlap.  The first call allocates the staging buffers.
+ */
+int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float dt,
+                 int64_t n, void* stream);
+
+/* sr_last_error -- message of the last failure on this thread ("" if none). */
+const char* sr_last_error(void);
+
+/* sr_launch_count -- number of kernels this library has launched so far
+ * (process-wide, all threads). */
+int64_t sr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SR_H */

@@ -1,0 +1,79 @@
+"""ctypes declarations of the C ABI in include/sr.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_double, c_float, c_int, c_int64, c_uint64, c_void_p, c_char_p
+
+from .build import LIB
+
+SR_OK, SR_ERR_ARG, SR_ERR_CUDA, SR_ERR_CAPACITY, SR_ERR_STATE, SR_ERR_RANGE = range(6)
+FIT_MODES = {"constrained": 0, "unconstrained": 1}
+EXPORTS = {
+    "perm": 0, "cell_start": 1, "cell_chunk_start": 2, "slot_pos": 3, "slot_idx": 4,
+    "chunk_meta": 5, "chunk_lo": 6, "chunk_hi": 7, "order": 8, "cost": 9, "counters": 10,
+}
+
+
+class SrParams(ctypes.Structure):
+    _fields_ = [("box", c_double), ("r_c", c_double), ("eps", c_double), ("sigma", c_double),
+                ("fit_mode", c_int), ("n_cells", c_int), ("sub_bits", c_int), ("reserved", c_int)]
+
+
+class SrPlanInfo(ctypes.Structure):
+    _fields_ = [("n_particles", c_int64), ("capacity", c_int64), ("n_volumes", c_int64),
+                ("total_cells", c_int64), ("max_chunks", c_int64), ("n_chunks", c_int64),
+                ("sub_bits", ctypes.c_int32), ("key_bits", ctypes.c_int32),
+                ("workers", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("coef", c_double * 6)]
+
+
+class SrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sr error {code}: {msg}")
+        self.code = code
+
+
+SIGNATURES = {
+    "sr_fit_poly": (c_int, [c_double, c_double, c_double, c_int, POINTER(c_double)]),
+    "sr_plan_create": (c_int, [POINTER(SrParams), c_int64, POINTER(c_void_p)]),
+    "sr_plan_batch": (c_int, [POINTER(SrParams), POINTER(c_int64), c_int, POINTER(c_void_p)]),
+    "sr_plan_destroy": (c_int, [c_void_p]),
+    "sr_plan_get_info": (c_int, [c_void_p, POINTER(SrPlanInfo)]),
+    "sr_plan_volume_info": (c_int, [c_void_p, c_int, POINTER(c_int64), POINTER(c_double),
+                                    POINTER(c_int), POINTER(c_double)]),
+    "sr_bin": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "sr_force": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sr_force_plain": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "sr_force_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_int, c_void_p]),
+    "sr_kick": (c_int, [c_int64, c_void_p, c_void_p, c_float, c_void_p]),
+    "sr_drift": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int64, c_void_p]),
+    "sr_invariants": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sr_plan_status": (c_int, [c_void_p, c_void_p]),
+    "sr_plan_copy": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p]),
+    "sr_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
+    "sr_last_error": (c_char_p, []),
+    "sr_launch_count": (c_int64, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libsr_b300.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not LIB.exists():
+            raise RuntimeError(f"{LIB.name} is not built; run __graft_entry__.build() first")
+        lib = ctypes.CDLL(str(LIB))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(code: int):
+    if code != SR_OK:
+        msg = load().sr_last_error().decode(errors="replace")
+        raise SrError(code, msg)

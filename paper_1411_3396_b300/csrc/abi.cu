@@ -1,0 +1,432 @@
+// C ABI: plan lifecycle, argument checking, error reporting and the thin
+// wrappers that enqueue the kernels of bin.cu, force.cu, plain.cu, kick.cu.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sr_internal.h"
+
+namespace sr {
+namespace {
+thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
+
+constexpr double kSideMargin = 1.0 + 1.0 / (1 << 20);   // cell side must exceed r_c by this factor
+constexpr double kCullMargin = 1.0 + 1.0 / 512.0;       // culling radius^2 relative margin
+
+template <class T>
+int dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    return SR_OK;
+}
+
+void free_plan(sr_plan* p) {
+    if (!p) return;
+    cudaFree(p->vols);
+    cudaFree(p->vol_part_start);
+    cudaFree(p->vol_cell_base);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(p->keys[k]);
+        cudaFree(p->vals[k]);
+        cudaFree(p->lpt_keys[k]);
+        cudaFree(p->lpt_vals[k]);
+    }
+    cudaFree(p->cell_start);
+    cudaFree(p->cell_nch);
+    cudaFree(p->ccs);
+    cudaFree(p->chunk_meta);
+    cudaFree(p->chunk_lo);
+    cudaFree(p->chunk_hi);
+    cudaFree(p->cost);
+    cudaFree(p->slot_pos);
+    cudaFree(p->slot_idx);
+    cudaFree(p->slot_g);
+    cudaFree(p->ctr);
+    cudaFree(p->inv_partials);
+    cudaFree(p->h_pos_dev);
+    cudaFree(p->h_vel_dev);
+    cudaFree(p->h_acc_dev);
+    radix_free(p->rs_particles);
+    radix_free(p->rs_chunks);
+    scan_free(p->scan_cells);
+    delete p;
+}
+
+int check_physics(const sr_params& q) {
+    if (!(q.r_c > 0) || !std::isfinite(q.r_c)) return set_error(SR_ERR_ARG, "r_c must be positive and finite");
+    if (!(q.eps > 0) || !std::isfinite(q.eps)) return set_error(SR_ERR_ARG, "eps must be positive and finite");
+    if (!(q.sigma > 0) || !std::isfinite(q.sigma)) return set_error(SR_ERR_ARG, "sigma must be positive and finite");
+    if (q.fit_mode != SR_FIT_CONSTRAINED && q.fit_mode != SR_FIT_UNCONSTRAINED)
+        return set_error(SR_ERR_ARG, "bad fit_mode");
+    if (q.reserved != 0) return set_error(SR_ERR_ARG, "reserved must be 0");
+    if (q.sub_bits < 0 || q.sub_bits > 8) return set_error(SR_ERR_ARG, "sub_bits must be in 0..8");
+    return SR_OK;
+}
+
+// Geometry and unit constants of one volume.
+int make_volume(const sr_params& q, const double coef[6], int b, int cell_base, VolDev* V, int* n_c_out) {
+    if (!(q.box > 2.0 * q.r_c) || !std::isfinite(q.box))
+        return set_error(SR_ERR_ARG, "box must be finite and exceed 2 r_c (unique minimum image)");
+    const double min_side = q.r_c * kSideMargin;
+    int n_c = q.n_cells;
+    if (n_c == 0) {
+        const double target = min_side > 4.0 ? min_side : 4.0;
+        n_c = (int)std::floor(q.box / target);
+        if (n_c < 1) n_c = 1;
+    }
+    if (n_c < 1) return set_error(SR_ERR_ARG, "n_cells must be >= 0");
+    if (q.box / n_c < min_side) return set_error(SR_ERR_ARG, "cell side L/n_cells must exceed r_c");
+    if ((long long)n_c << b >= (1ll << 23)) return set_error(SR_ERR_ARG, "n_cells * 2^sub_bits too large");
+    std::memset(V, 0, sizeof(VolDev));
+    V->box = q.box;
+    V->n_c = n_c;
+    V->M = n_c << b;
+    V->sub_bits = b;
+    V->cell_base = cell_base;
+    const double h = q.box / V->M;
+    V->h = h;
+    const double h2 = h * h;
+    const double e64 = q.eps * q.eps;
+    V->eps2u = (float)(e64 / h2);
+    V->rc2u = (float)((q.r_c * q.r_c + e64) / h2);
+    const double rcm2 = (q.r_c * q.r_c / h2) * kCullMargin;
+    V->rcm2u = (float)rcm2;
+    V->rcm = (float)std::sqrt(rcm2);
+    V->scale_a = (float)(1.0 / h2);
+    V->scale_g = (float)(1.0 / (h2 * h));
+    // q(x) = h^3 p(h^2 (x - e_u)) expanded in powers of x.
+    const double eu = e64 / h2;
+    double qm[6];
+    for (int m = 0; m <= 5; ++m) {
+        double s = 0.0;
+        for (int k = m; k <= 5; ++k) {
+            double binom = 1.0;
+            for (int t = 0; t < m; ++t) binom = binom * (k - t) / (t + 1);
+            s += coef[k] * std::pow(h2, k) * binom * std::pow(-eu, k - m);
+        }
+        qm[m] = h2 * h * s;
+    }
+    for (int m = 0; m <= 5; ++m) V->nq[m] = (float)(-qm[m]);
+    for (int m = 0; m < 5; ++m) V->ndq[m] = (float)(-(m + 1) * qm[m + 1]);
+    *n_c_out = n_c;
+    return SR_OK;
+}
+
+int build_plan(const sr_params* params, const long long* n, int n_vol, bool batch, sr_plan** out) {
+    *out = nullptr;
+    if (!params || !n || n_vol < 1) return set_error(SR_ERR_ARG, "null parameters");
+    int rc = check_physics(params[0]);
+    if (rc) return rc;
+    for (int v = 1; v < n_vol; ++v) {
+        const sr_params& q = params[v];
+        if ((rc = check_physics(q))) return rc;
+        if (q.r_c != params[0].r_c || q.eps != params[0].eps || q.sigma != params[0].sigma ||
+            q.fit_mode != params[0].fit_mode || q.sub_bits != params[0].sub_bits)
+            return set_error(SR_ERR_ARG, "batch volumes must share r_c, eps, sigma, fit_mode, sub_bits");
+    }
+    long long cap = 0;
+    for (int v = 0; v < n_vol; ++v) {
+        if (n[v] < (batch ? 0 : 1)) return set_error(SR_ERR_ARG, "particle count must be positive");
+        cap += n[v];
+    }
+    if (cap < 1 || cap > (1ll << 30)) return set_error(SR_ERR_ARG, "particle count must be in [1, 2^30]");
+
+    sr_plan* p = new sr_plan();
+    p->phys = params[0];
+    p->n_vol = n_vol;
+    p->capacity = cap;
+    p->sub_bits = params[0].sub_bits ? params[0].sub_bits : 6;
+    if ((rc = fit_poly(params[0].r_c, params[0].sigma, params[0].eps, params[0].fit_mode, p->coef))) {
+        delete p;
+        return rc;
+    }
+    long long cells = 0, start = 0;
+    std::vector<long long> part_start(n_vol + 1);
+    std::vector<int> cell_base(n_vol + 1);
+    for (int v = 0; v < n_vol; ++v) {
+        VolDev V;
+        int n_c = 0;
+        if ((rc = make_volume(params[v], p->coef, p->sub_bits, (int)cells, &V, &n_c))) { delete p; return rc; }
+        V.part_start = start;
+        V.part_end = start + n[v];
+        part_start[v] = start;
+        cell_base[v] = (int)cells;
+        start += n[v];
+        cells += (long long)n_c * n_c * n_c;
+        if (cells >= (1ll << 30)) { delete p; return set_error(SR_ERR_ARG, "too many cells"); }
+        p->vols_h.push_back(V);
+        p->vol_n.push_back(n[v]);
+    }
+    part_start[n_vol] = start;
+    cell_base[n_vol] = (int)cells;
+    p->total_cells = cells;
+    int cell_bits = 0;
+    while ((1ll << cell_bits) < cells) ++cell_bits;
+    p->key_bits = cell_bits + 3 * p->sub_bits;
+    p->max_chunks = (cap + kChunk - 1) / kChunk + (cap < cells ? cap : cells);
+    if (p->max_chunks * kChunk >= (1ll << 31)) { delete p; return set_error(SR_ERR_CAPACITY, "too many slots"); }
+
+    cudaError_t ge = cudaGetDevice(&p->device);
+    if (ge == cudaSuccess) ge = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (ge != cudaSuccess) {
+        delete p;
+        return cuda_fail(ge, "device query");
+    }
+    const long long mc = p->max_chunks, slots = mc * kChunk;
+#define SR_ALLOC(ptr, cnt)                                 \
+    do {                                                   \
+        if ((rc = dalloc(&(ptr), (size_t)(cnt)))) {        \
+            free_plan(p);                                  \
+            return rc;                                     \
+        }                                                  \
+    } while (0)
+    SR_ALLOC(p->vols, n_vol);
+    SR_ALLOC(p->vol_part_start, n_vol + 1);
+    SR_ALLOC(p->vol_cell_base, n_vol + 1);
+    for (int k = 0; k < 2; ++k) {
+        SR_ALLOC(p->keys[k], cap);
+        SR_ALLOC(p->vals[k], cap);
+        SR_ALLOC(p->lpt_keys[k], mc);
+        SR_ALLOC(p->lpt_vals[k], mc);
+    }
+    SR_ALLOC(p->cell_start, cells + 1);
+    SR_ALLOC(p->cell_nch, cells + 1);
+    SR_ALLOC(p->ccs, cells + 1);
+    SR_ALLOC(p->chunk_meta, mc);
+    SR_ALLOC(p->chunk_lo, mc);
+    SR_ALLOC(p->chunk_hi, mc);
+    SR_ALLOC(p->cost, mc);
+    SR_ALLOC(p->slot_pos, slots);
+    SR_ALLOC(p->slot_idx, slots);
+    SR_ALLOC(p->slot_g, slots);
+    SR_ALLOC(p->ctr, 1);
+    SR_ALLOC(p->inv_partials, (size_t)kInvBlocks * 7);
+#undef SR_ALLOC
+    if ((rc = radix_alloc(p->rs_particles, cap)) || (rc = radix_alloc(p->rs_chunks, mc)) ||
+        (rc = scan_alloc(p->scan_cells, cells + 1))) {
+        free_plan(p);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(p->vols, p->vols_h.data(), sizeof(VolDev) * n_vol, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->vol_part_start, part_start.data(), sizeof(long long) * (n_vol + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->vol_cell_base, cell_base.data(), sizeof(int) * (n_vol + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->ctr, 0, sizeof(Counters));
+    // an empty ccs table until the first sr_bin: zero chunks
+    if (e == cudaSuccess) e = cudaMemset(p->ccs, 0, sizeof(int) * (cells + 1));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "plan initialisation");
+    }
+    if ((rc = force_occupancy(p))) {
+        free_plan(p);
+        return rc;
+    }
+    p->order = p->lpt_vals[0];
+    *out = p;
+    return SR_OK;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return SR_ERR_CUDA;
+}
+
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+}  // namespace sr
+
+using namespace sr;
+
+extern "C" {
+
+int sr_fit_poly(double r_c, double sigma, double eps, int mode, double c_out[6]) {
+    return fit_poly(r_c, sigma, eps, mode, c_out);
+}
+
+int sr_plan_create(const sr_params* params, int64_t n_max, sr_plan** out) {
+    if (!out) return set_error(SR_ERR_ARG, "out is null");
+    long long n = n_max;
+    return build_plan(params, &n, 1, false, out);
+}
+
+int sr_plan_batch(const sr_params* params, const int64_t* n, int n_vol, sr_plan** out) {
+    if (!out) return set_error(SR_ERR_ARG, "out is null");
+    if (!n || n_vol < 1) return set_error(SR_ERR_ARG, "bad volume list");
+    std::vector<long long> nn(n, n + n_vol);
+    return build_plan(params, nn.data(), n_vol, true, out);
+}
+
+int sr_plan_destroy(sr_plan* plan) {
+    if (!plan) return SR_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return SR_OK;
+}
+
+int sr_plan_get_info(sr_plan* p, sr_plan_info* info) {
+    if (!p || !info) return set_error(SR_ERR_ARG, "null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_particles = p->binned ? p->n_binned : p->capacity;
+    info->capacity = p->capacity;
+    info->n_volumes = p->n_vol;
+    info->total_cells = p->total_cells;
+    info->max_chunks = p->max_chunks;
+    int nch = 0;
+    SR_CUDA_CHECK(cudaMemcpy(&nch, p->ccs + p->total_cells, sizeof(int), cudaMemcpyDeviceToHost));
+    info->n_chunks = nch;
+    info->sub_bits = p->sub_bits;
+    info->key_bits = p->key_bits;
+    info->workers = p->force_blocks * p->warps_per_block;
+    info->warps_per_block = p->warps_per_block;
+    for (int k = 0; k < 6; ++k) info->coef[k] = p->coef[k];
+    return SR_OK;
+}
+
+int sr_plan_volume_info(const sr_plan* p, int v, int64_t* n, double* box, int* n_cells, double* h) {
+    if (!p || v < 0 || v >= p->n_vol) return set_error(SR_ERR_ARG, "bad plan or volume index");
+    if (n) *n = p->vol_n[v];
+    if (box) *box = p->vols_h[v].box;
+    if (n_cells) *n_cells = p->vols_h[v].n_c;
+    if (h) *h = p->vols_h[v].h;
+    return SR_OK;
+}
+
+int sr_bin(sr_plan* p, const double* pos, int64_t n, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!pos && n > 0) return set_error(SR_ERR_ARG, "pos is null");
+    if (n < 0) return set_error(SR_ERR_ARG, "n must be >= 0");
+    if (n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    if (p->n_vol > 1 && n != p->capacity)
+        return set_error(SR_ERR_CAPACITY, "a batch plan bins exactly the sum of its volume counts");
+    int rc = launch_bin(p, pos, n, as_stream(stream));
+    if (rc) return rc;
+    p->n_binned = n;
+    p->binned = true;
+    return SR_OK;
+}
+
+int sr_force(sr_plan* p, float* acc, unsigned long long* pair_count, int* per_particle, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->binned) return set_error(SR_ERR_STATE, "sr_force before sr_bin");
+    if (!acc) return set_error(SR_ERR_ARG, "acc is null");
+    return launch_force(p, acc, pair_count, per_particle, as_stream(stream));
+}
+
+int sr_force_plain(sr_plan* p, float* acc, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_plain before sr_bin");
+    if (!acc) return set_error(SR_ERR_ARG, "acc is null");
+    return launch_force_plain(p, acc, as_stream(stream));
+}
+
+int sr_force_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int accumulate, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_vjp before sr_bin");
+    if (!g_acc || !g_pos) return set_error(SR_ERR_ARG, "null cotangent pointer");
+    return launch_vjp(p, g_acc, g_pos, g_scale, accumulate ? 1 : 0, as_stream(stream));
+}
+
+int sr_kick(int64_t n, const float* acc, float* vel, float dt, void* stream) {
+    if (n < 0) return set_error(SR_ERR_ARG, "n must be >= 0");
+    if (n > 0 && (!acc || !vel)) return set_error(SR_ERR_ARG, "null pointer");
+    return launch_kick(n, acc, vel, dt, as_stream(stream));
+}
+
+int sr_drift(sr_plan* p, double* pos, const float* vel, double dt, int64_t n, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (n < 0) return set_error(SR_ERR_ARG, "n must be >= 0");
+    if (n > 0 && (!pos || !vel)) return set_error(SR_ERR_ARG, "null pointer");
+    if (n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    return launch_drift(p, pos, vel, dt, n, as_stream(stream));
+}
+
+int sr_invariants(sr_plan* p, int64_t n, const float* vel, const float* acc, double* out, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!out) return set_error(SR_ERR_ARG, "out is null");
+    if (n < 0) return set_error(SR_ERR_ARG, "n must be >= 0");
+    if (n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    return launch_invariants(n, vel, acc, out, p->inv_partials, as_stream(stream));
+}
+
+int sr_plan_status(sr_plan* p, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    long long err = 0;
+    cudaStream_t st = as_stream(stream);
+    SR_CUDA_CHECK(cudaMemcpyAsync(&err, &p->ctr->err, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SR_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (err & 1) {
+        SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->err, 0, sizeof(long long), st));
+        SR_CUDA_CHECK(cudaStreamSynchronize(st));
+        return set_error(SR_ERR_RANGE, "sr_bin saw a non-finite position or one outside [-L, 2L)");
+    }
+    return SR_OK;
+}
+
+int sr_plan_copy(sr_plan* p, int which, void* dst, int64_t bytes, void* stream) {
+    if (!p || !dst || bytes < 0) return set_error(SR_ERR_ARG, "null argument");
+    const void* src = nullptr;
+    long long avail = 0;
+    const long long mc = p->max_chunks, cells = p->total_cells;
+    switch (which) {
+        case SR_EXPORT_PERM: src = p->vals[p->sorted]; avail = 4 * p->capacity; break;
+        case SR_EXPORT_CELL_START: src = p->cell_start; avail = 4 * (cells + 1); break;
+        case SR_EXPORT_CELL_CHUNK_START: src = p->ccs; avail = 4 * (cells + 1); break;
+        case SR_EXPORT_SLOT_POS: src = p->slot_pos; avail = 16 * mc * kChunk; break;
+        case SR_EXPORT_SLOT_IDX: src = p->slot_idx; avail = 4 * mc * kChunk; break;
+        case SR_EXPORT_CHUNK_META: src = p->chunk_meta; avail = 16 * mc; break;
+        case SR_EXPORT_CHUNK_LO: src = p->chunk_lo; avail = 16 * mc; break;
+        case SR_EXPORT_CHUNK_HI: src = p->chunk_hi; avail = 16 * mc; break;
+        case SR_EXPORT_ORDER: src = p->order; avail = 4 * mc; break;
+        case SR_EXPORT_COST: src = p->cost; avail = 4 * mc; break;
+        case SR_EXPORT_COUNTERS: src = p->ctr; avail = sizeof(Counters); break;
+        default: return set_error(SR_ERR_ARG, "unknown export selector");
+    }
+    if (bytes > avail) return set_error(SR_ERR_ARG, "bytes exceeds the array size");
+    if (bytes == 0) return SR_OK;
+    SR_CUDA_CHECK(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, as_stream(stream)));
+    return SR_OK;
+}
+
+int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt, int64_t n, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!pos || !vel) return set_error(SR_ERR_ARG, "null host buffer");
+    if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    cudaStream_t st = as_stream(stream);
+    int rc;
+    if (!p->h_pos_dev) {
+        if ((rc = dalloc(&p->h_pos_dev, (size_t)p->capacity * 3)) || (rc = dalloc(&p->h_vel_dev, (size_t)p->capacity * 4)) ||
+            (rc = dalloc(&p->h_acc_dev, (size_t)p->capacity * 4)))
+            return rc;
+    }
+    SR_CUDA_CHECK(cudaMemcpyAsync(p->h_pos_dev, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    SR_CUDA_CHECK(cudaMemcpyAsync(p->h_vel_dev, vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, st));
+    if ((rc = sr_bin(p, p->h_pos_dev, n, stream))) return rc;
+    if ((rc = launch_force(p, p->h_acc_dev, nullptr, nullptr, st))) return rc;
+    if ((rc = launch_kick(n, p->h_acc_dev, p->h_vel_dev, dt, st))) return rc;
+    SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->h_vel_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
+    if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
+    SR_CUDA_CHECK(cudaStreamSynchronize(st));
+    return SR_OK;
+}
+
+const char* sr_last_error(void) { return g_last_error.c_str(); }
+
+int64_t sr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Binning: bit-exact cells, sub-cell Morton order and 32-particle chunks.
+// This is step 1 of the paper's short-range timestep (Sec. 2.1: partition
+// the volume into overlapping blocks of active particles whose passive
+// neighbours lie within the cutoff).
+//
+// Spec (per volume of side L, n_c cells per axis, b sub-cell bits,
+// M = n_c 2^b fine cells per axis, h = L / M in binary64):
+//   fold      x < 0 -> x + L, then x >= L -> x - L     (inputs in [-L, 2L))
+//   t = x / h (binary64, round to nearest), q = min(floor(t), M - 1)
+//   cell = q >> b, sub = q & (2^b - 1), global cell id volume-major,
+//   key = (cell << 3b) | morton(sub);  stable sort by key (LSD radix)
+//   chunks = runs of <= 32 consecutive particles inside a cell
+//   anchor qA = q of the chunk's first particle, offset = binary32(t - qA)
+#include "sr_internal.h"
+
+namespace sr {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned long long spread3(unsigned v) {
+    unsigned long long x = v & 0x3ffu;               // up to 10 bits
+    x = (x | (x << 16)) & 0x030000FFull;
+    x = (x | (x << 8)) & 0x0300F00Full;
+    x = (x | (x << 4)) & 0x030C30C3ull;
+    x = (x | (x << 2)) & 0x09249249ull;
+    return x;
+}
+
+__device__ __forceinline__ int volume_of_row(long long i, const long long* __restrict__ part_start,
+                                             int n_vol) {
+    // largest v with part_start[v] <= i  (part_start[0] = 0)
+    int lo = 0, hi = n_vol;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (part_start[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int volume_of_cell(int cell, const int* __restrict__ cell_base, int n_vol) {
+    int lo = 0, hi = n_vol;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cell_base[mid] <= cell) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Fine-grid coordinate of one axis; flags non-finite / out-of-range input.
+__device__ __forceinline__ void fine_axis(double x, double box, double h, int M, double& t, int& q,
+                                          bool& bad) {
+    if (!(x >= -box && x < 2.0 * box)) {  // also catches NaN
+        bad = true;
+        x = 0.0;
+    }
+    if (x < 0.0) x = x + box;
+    if (x >= box) x = x - box;
+    t = x / h;
+    int qq = (int)floor(t);
+    if (qq > M - 1) qq = M - 1;
+    if (qq < 0) qq = 0;
+    q = qq;
+}
+
+__global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, int n,
+                                              const VolDev* __restrict__ vols,
+                                              const long long* __restrict__ part_start, int n_vol,
+                                              int b, unsigned long long* __restrict__ keys,
+                                              int* __restrict__ vals, Counters* ctr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int v = n_vol > 1 ? volume_of_row(i, part_start, n_vol) : 0;
+    const VolDev& V = vols[v];
+    bool bad = false;
+    int q[3];
+    double t[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) fine_axis(pos[3ll * i + ax], V.box, V.h, V.M, t[ax], q[ax], bad);
+    const int mask = (1 << b) - 1;
+    const int cell = V.cell_base + ((q[2] >> b) * V.n_c + (q[1] >> b)) * V.n_c + (q[0] >> b);
+    const unsigned long long m = spread3(q[0] & mask) | (spread3(q[1] & mask) << 1) |
+                                 (spread3(q[2] & mask) << 2);
+    keys[i] = ((unsigned long long)cell << (3 * b)) | m;
+    vals[i] = i;
+    if (bad) atomicOr((unsigned long long*)&ctr->err, 1ull);
+}
+
+__global__ void __launch_bounds__(256) k_cell_bounds(const unsigned long long* __restrict__ keys, int n,
+                                                     int shift, int total_cells, int* __restrict__ cell_start) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > n) return;
+    const int c_prev = p > 0 ? (int)(keys[p - 1] >> shift) : -1;
+    const int c_cur = p < n ? (int)(keys[p] >> shift) : total_cells;
+    for (int c = c_prev + 1; c <= c_cur; ++c) cell_start[c] = p;
+}
+
+__global__ void __launch_bounds__(256) k_cell_nch(const int* __restrict__ cell_start, int total_cells,
+                                                  int* __restrict__ nch) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > total_cells) return;
+    nch[c] = c < total_cells ? (cell_start[c + 1] - cell_start[c] + kChunk - 1) / kChunk : 0;
+}
+
+// One warp per chunk: slot positions / indices, anchor, bounding box.
+__global__ void __launch_bounds__(256) k_chunk_fill(
+    const double* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ cell_start,
+    const int* __restrict__ ccs, int total_cells, const VolDev* __restrict__ vols,
+    const int* __restrict__ vol_cell_base, int n_vol, int b, float4* __restrict__ slot_pos,
+    int* __restrict__ slot_idx, int4* __restrict__ chunk_meta, float4* __restrict__ chunk_lo,
+    float4* __restrict__ chunk_hi) {
+    const int lane = threadIdx.x & 31;
+    const int n_chunks = ccs[total_cells];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_chunks; k += warps) {
+        int lo = 0, hi = total_cells;              // ccs[lo] <= k < ccs[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ccs[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int cell = lo;
+        const int r0 = (k - ccs[cell]) * kChunk;
+        const int n_cell = cell_start[cell + 1] - cell_start[cell];
+        const int rank = r0 + lane;
+        const bool valid = rank < n_cell;
+        const int v = n_vol > 1 ? volume_of_cell(cell, vol_cell_base, n_vol) : 0;
+        const VolDev& V = vols[v];
+        int orig = -1;
+        int q[3] = {0, 0, 0};
+        double t[3] = {0.0, 0.0, 0.0};
+        if (valid) {
+            orig = perm[cell_start[cell] + rank];
+            bool bad = false;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) fine_axis(pos[3ll * orig + ax], V.box, V.h, V.M, t[ax], q[ax], bad);
+        }
+        int qa[3];
+        float off[3], bl[3], bh[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            qa[ax] = __shfl_sync(kFull, q[ax], 0);
+            off[ax] = valid ? __double2float_rn(t[ax] - (double)qa[ax]) : kPad;
+            bl[ax] = valid ? off[ax] : __int_as_float(0x7f800000);   // +inf
+            bh[ax] = valid ? off[ax] : __int_as_float(0xff800000);   // -inf
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                bl[ax] = fminf(bl[ax], __shfl_xor_sync(kFull, bl[ax], o));
+                bh[ax] = fmaxf(bh[ax], __shfl_xor_sync(kFull, bh[ax], o));
+            }
+        }
+        const long long slot = (long long)k * kChunk + lane;
+        slot_pos[slot] = make_float4(off[0], off[1], off[2], valid ? 1.0f : 0.0f);
+        slot_idx[slot] = orig;
+        if (lane == 0) {
+            const int cnt = min(kChunk, n_cell - r0);
+            chunk_meta[k] = make_int4(qa[0], qa[1], qa[2], v);
+            chunk_lo[k] = make_float4(bl[0], bl[1], bl[2], __int_as_float(cnt));
+            chunk_hi[k] = make_float4(bh[0], bh[1], bh[2], 0.0f);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st) {
+    const int b = p->sub_bits;
+    const int ni = (int)n;
+    if (ni > 0) {
+        k_keys<<<(ni + 255) / 256, 256, 0, st>>>(pos, ni, p->vols, p->vol_part_start, p->n_vol, b,
+                                                 p->keys[0], p->vals[0], p->ctr);
+        SR_LAUNCH_CHECK("k_keys");
+    }
+    int which = 0;
+    int rc = radix_sort_pairs(p->keys, p->vals, ni, p->key_bits, p->rs_particles, st, &which);
+    if (rc) return rc;
+    p->sorted = which;
+    const int tc = (int)p->total_cells;
+    k_cell_bounds<<<(ni + 1 + 255) / 256, 256, 0, st>>>(p->keys[which], ni, 3 * b, tc, p->cell_start);
+    SR_LAUNCH_CHECK("k_cell_bounds");
+    k_cell_nch<<<(tc + 1 + 255) / 256, 256, 0, st>>>(p->cell_start, tc, p->cell_nch);
+    SR_LAUNCH_CHECK("k_cell_nch");
+    rc = exclusive_scan(p->cell_nch, p->ccs, tc + 1, p->scan_cells, st);
+    if (rc) return rc;
+    long long want = (p->max_chunks + 7) / 8;
+    long long cap = (long long)p->sm_count * 16;
+    const int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    k_chunk_fill<<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, tc, p->vols,
+                                         p->vol_cell_base, p->n_vol, b, p->slot_pos, p->slot_idx,
+                                         p->chunk_meta, p->chunk_lo, p->chunk_hi);
+    SR_LAUNCH_CHECK("k_chunk_fill");
+    return launch_cost_and_order(p, st);
+}
+
+}  // namespace sr

@@ -1,0 +1,121 @@
+// Elementwise kernels that close the step: the kick v += a dt, the drift
+// x <- fold(x + v dt), and deterministic binary64 global sums (momentum,
+// net force, kinetic energy) used as run-health invariants.
+#include "sr_internal.h"
+
+namespace sr {
+namespace {
+
+__global__ void __launch_bounds__(256) k_kick(long long n, const float4* __restrict__ acc,
+                                              float4* __restrict__ vel, float dt) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 a = acc[i];
+        float4 v = vel[i];
+        v.x = fmaf(a.x, dt, v.x);
+        v.y = fmaf(a.y, dt, v.y);
+        v.z = fmaf(a.z, dt, v.z);
+        vel[i] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_drift(long long n, double* __restrict__ pos,
+                                               const float4* __restrict__ vel, double dt,
+                                               const VolDev* __restrict__ vols,
+                                               const long long* __restrict__ part_start, int n_vol) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int lo = 0, hi = n_vol;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (part_start[mid] <= i) lo = mid; else hi = mid;
+        }
+        const double box = vols[lo].box;
+        const float4 v = vel[i];
+        const double vv[3] = {(double)v.x, (double)v.y, (double)v.z};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            double x = pos[3 * i + ax] + vv[ax] * dt;
+            if (x < 0.0) x = x + box;
+            if (x >= box) x = x - box;
+            pos[3 * i + ax] = x;
+        }
+    }
+}
+
+// Stage 1: each block reduces a fixed, contiguous range of rows (so the
+// association order depends only on n), writing 7 partial sums.
+__global__ void __launch_bounds__(256) k_inv_partial(long long n, const float4* __restrict__ vel,
+                                                     const float4* __restrict__ acc,
+                                                     double* __restrict__ partials) {
+    __shared__ double sh[7][256];
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long b0 = (long long)blockIdx.x * per;
+    const long long b1 = b0 + per < n ? b0 + per : n;
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        if (vel) {
+            const float4 v = vel[i];
+            s[0] += v.x; s[1] += v.y; s[2] += v.z;
+            s[6] += 0.5 * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        }
+        if (acc) {
+            const float4 a = acc[i];
+            s[3] += a.x; s[4] += a.y; s[5] += a.z;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) partials[(long long)blockIdx.x * 7 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_inv_final(const double* __restrict__ partials, int blocks, double* __restrict__ out) {
+    if (threadIdx.x < 7) {
+        double s = 0.0;
+        for (int b = 0; b < blocks; ++b) s += partials[(long long)b * 7 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+int grid_for(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    return (int)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+int launch_kick(long long n, const float* acc, float* vel, float dt, cudaStream_t st) {
+    if (n == 0) return SR_OK;
+    k_kick<<<grid_for(n), 256, 0, st>>>(n, reinterpret_cast<const float4*>(acc), reinterpret_cast<float4*>(vel), dt);
+    SR_LAUNCH_CHECK("k_kick");
+    return SR_OK;
+}
+
+int launch_drift(sr_plan* p, double* pos, const float* vel, double dt, long long n, cudaStream_t st) {
+    if (n == 0) return SR_OK;
+    k_drift<<<grid_for(n), 256, 0, st>>>(n, pos, reinterpret_cast<const float4*>(vel), dt, p->vols,
+                                         p->vol_part_start, p->n_vol);
+    SR_LAUNCH_CHECK("k_drift");
+    return SR_OK;
+}
+
+int launch_invariants(long long n, const float* vel, const float* acc, double* out, double* partials,
+                      cudaStream_t st) {
+    k_inv_partial<<<kInvBlocks, 256, 0, st>>>(n, reinterpret_cast<const float4*>(vel),
+                                              reinterpret_cast<const float4*>(acc), partials);
+    SR_LAUNCH_CHECK("k_inv_partial");
+    k_inv_final<<<1, 32, 0, st>>>(partials, kInvBlocks, out);
+    SR_LAUNCH_CHECK("k_inv_final");
+    return SR_OK;
+}
+
+}  // namespace sr

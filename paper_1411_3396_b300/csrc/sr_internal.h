@@ -1,0 +1,173 @@
+// Internal declarations shared by the library's CUDA/C++ sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sr.h"
+
+namespace sr {
+
+constexpr int kChunk = 32;          // particles per chunk = lanes per warp
+constexpr float kPad = 1.0e30f;     // coordinate of an empty slot: never within r_c
+constexpr int kScanItems = 8;       // items per thread in scans / radix passes
+constexpr int kScanThreads = 256;
+constexpr int kScanTile = kScanItems * kScanThreads;
+constexpr int kRadixBits = 8;
+constexpr int kRadixBuckets = 1 << kRadixBits;
+
+// Per-volume constants, device resident, read once per work item.
+// Lengths inside kernels are in units of the fine grid h = L / (n_c 2^b).
+struct VolDev {
+    double box;          // L
+    double h;            // fine cell side, L / M
+    long long part_start;  // first caller row of the volume
+    long long part_end;
+    int n_c;             // cells per axis
+    int M;               // fine cells per axis, n_c << sub_bits
+    int cell_base;       // global id of the volume's first cell
+    int sub_bits;
+    float eps2u;         // binary32(eps^2 / h^2)
+    float rc2u;          // binary32((r_c^2 + eps^2) / h^2): in-range iff s' < rc2u
+    float rcm2u;         // culling radius^2 (r_c^2/h^2 with a relative margin)
+    float rcm;           // its square root
+    float scale_a;       // 1/h^2: unit sums -> accelerations
+    float scale_g;       // 1/h^3: unit sums -> position cotangents
+    float nq[6];         // -q(x) = sum nq[m] x^m, x = s' (units); f_u = r^3 - q(x)
+    float ndq[5];        // -q'(x) = sum ndq[m] x^m
+    float pad0;
+};
+
+// Device-side counters (one per plan).
+struct Counters {
+    long long queue;          // next work item of the persistent kernels
+    long long err;            // bit 0: bad position seen by sr_bin
+    unsigned long long cost_total;
+    long long reserved[5];
+};
+
+struct ScanScratch {
+    std::vector<int*> partials;   // one buffer per recursion level
+    std::vector<int> sizes;
+};
+
+struct RadixScratch {
+    int* hist = nullptr;          // kRadixBuckets * n_tiles
+    int* hist_scan = nullptr;
+    int max_tiles = 0;
+    ScanScratch scan;
+};
+
+}  // namespace sr
+
+struct sr_plan {
+    int device = 0;
+    int n_vol = 0;
+    long long capacity = 0;
+    long long n_binned = 0;
+    bool binned = false;
+    int sub_bits = 6;
+    int key_bits = 0;
+    long long total_cells = 0;
+    long long max_chunks = 0;
+    double coef[6] = {0, 0, 0, 0, 0, 0};
+    sr_params phys{};
+    std::vector<sr::VolDev> vols_h;
+    std::vector<long long> vol_n;
+
+    // device workspace
+    sr::VolDev* vols = nullptr;
+    long long* vol_part_start = nullptr;   // n_vol + 1
+    int* vol_cell_base = nullptr;          // n_vol + 1
+    unsigned long long* keys[2] = {nullptr, nullptr};
+    int* vals[2] = {nullptr, nullptr};
+    int sorted = 0;                        // buffer index holding the sorted result
+    int* cell_start = nullptr;             // total_cells + 1
+    int* cell_nch = nullptr;               // total_cells + 1
+    int* ccs = nullptr;                    // cell -> first chunk, total_cells + 1
+    int4* chunk_meta = nullptr;            // anchor qx, qy, qz, volume
+    float4* chunk_lo = nullptr;            // bbox min, w = count (int bits)
+    float4* chunk_hi = nullptr;
+    unsigned* cost = nullptr;
+    unsigned long long* lpt_keys[2] = {nullptr, nullptr};
+    int* lpt_vals[2] = {nullptr, nullptr};
+    int* order = nullptr;                  // points into lpt_vals[sorted_lpt]
+    float4* slot_pos = nullptr;
+    int* slot_idx = nullptr;
+    float4* slot_g = nullptr;
+    sr::Counters* ctr = nullptr;
+    double* inv_partials = nullptr;
+    sr::RadixScratch rs_particles;
+    sr::RadixScratch rs_chunks;
+    sr::ScanScratch scan_cells;
+
+    // staging for sr_step_host
+    double* h_pos_dev = nullptr;
+    float* h_vel_dev = nullptr;
+    float* h_acc_dev = nullptr;
+
+    int sm_count = 0;
+    int force_blocks = 0;
+    int vjp_blocks = 0;
+    int count_blocks = 0;
+    int warps_per_block = 8;
+};
+
+namespace sr {
+
+// error handling ------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+void note_launch(int k = 1);
+#define SR_CUDA_CHECK(call)                                  \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return sr::cuda_fail(_e, #call); \
+    } while (0)
+#define SR_LAUNCH_CHECK(what)                                \
+    do {                                                     \
+        sr::note_launch();                                   \
+        cudaError_t _e = cudaGetLastError();                 \
+        if (_e != cudaSuccess) return sr::cuda_fail(_e, what); \
+    } while (0)
+
+// host-side fit (fit.cpp)
+int fit_poly(double rc, double sigma, double eps, int mode, double c[6]);
+
+// scans and sorts (radix.cu)
+int scan_alloc(ScanScratch& s, long long n);
+void scan_free(ScanScratch& s);
+int exclusive_scan(const int* in, int* out, int n, ScanScratch& s, cudaStream_t st);
+int radix_alloc(RadixScratch& r, long long n);
+void radix_free(RadixScratch& r);
+// Sorts (keys[0], vals[0]) stably by the low key_bits bits; returns in *which
+// the index (0/1) of the buffer pair that holds the result.
+int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_bits,
+                     RadixScratch& r, cudaStream_t st, int* which);
+
+// binning (bin.cu)
+int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st);
+
+// force, cost, order, vjp (force.cu)
+int launch_cost_and_order(sr_plan* p, cudaStream_t st);
+int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_particle,
+                 cudaStream_t st);
+int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int accumulate,
+               cudaStream_t st);
+int force_occupancy(sr_plan* p);
+
+// plain kernel (plain.cu)
+int launch_force_plain(sr_plan* p, float* acc, cudaStream_t st);
+
+// elementwise (kick.cu)
+int launch_kick(long long n, const float* acc, float* vel, float dt, cudaStream_t st);
+int launch_drift(sr_plan* p, double* pos, const float* vel, double dt, long long n,
+                 cudaStream_t st);
+int launch_invariants(long long n, const float* vel, const float* acc, double* out,
+                      double* partials, cudaStream_t st);
+constexpr int kInvBlocks = 1184;   // 8 * 148
+
+}  // namespace sr

@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry
+point include/sr.h declares; host-only entry points work on the CPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import fit as ofit
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_3396_b300 import build
+    path = build()
+    return ctypes.CDLL(str(path))
+
+
+def declared_functions():
+    text = (ROOT / "include" / "sr.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sr_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("sr_bin", "sr_force", "sr_kick", "sr_force_vjp", "sr_fit_poly",
+                 "sr_plan_create", "sr_plan_batch", "sr_plan_destroy", "sr_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("mode,mname", [(0, "constrained"), (1, "unconstrained")])
+@pytest.mark.parametrize("rc,sigma,eps", [(3.0, 0.8, 0.1), (3.0, 0.8, 0.05), (2.5, 0.6, 0.02)])
+def test_library_fit_matches_oracle(lib, mode, mname, rc, sigma, eps):
+    f = lib.sr_fit_poly
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = (ctypes.c_double * 6)()
+    assert f(rc, sigma, eps, mode, out) == 0
+    got = np.array(out[:]) * (rc * rc) ** np.arange(6)
+    ref = ofit.fit_poly(rc, sigma, eps, mname) * (rc * rc) ** np.arange(6)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_fit_rejects_bad_arguments(lib):
+    f = lib.sr_fit_poly
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    out = (ctypes.c_double * 6)()
+    assert f(-1.0, 0.8, 0.1, 0, out) == 1
+    assert f(3.0, 0.0, 0.1, 0, out) == 1
+    assert f(3.0, 0.8, 0.1, 7, out) == 1
+    lib.sr_last_error.restype = ctypes.c_char_p
+    assert b"bad" in lib.sr_last_error()
+
+
+def test_product_path_does_not_reference_the_oracle():
+    pkg = ROOT / "paper_1411_3396_b300"
+    for p in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cpp")) + \
+            list(pkg.rglob("*.h")):
+        assert "oracle" not in p.read_text(), p

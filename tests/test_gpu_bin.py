@@ -1,0 +1,107 @@
+"""sr_bin on the GPU is bit-exact against the oracle's binning spec."""
+import numpy as np
+import pytest
+
+from workloads import configs as wc
+from workloads import generators as gen
+
+from helpers import make_plan, oracle_binning, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _run_bin(vols, params, **kw):
+    pos = np.concatenate([p for p, _ in vols])
+    plan = make_plan(vols, params, **kw)
+    plan.bin(torch.from_numpy(pos).cuda())
+    torch.cuda.synchronize()
+    return plan
+
+
+def _compare(plan, vols):
+    B = oracle_binning(plan, vols)
+    info = plan.info()
+    assert info["n_chunks"] == B["n_chunks"]
+    np.testing.assert_array_equal(to_np(plan.export("perm")), B["perm"])
+    np.testing.assert_array_equal(to_np(plan.export("cell_start")), B["cell_start"])
+    np.testing.assert_array_equal(to_np(plan.export("cell_chunk_start")), B["cell_chunk_start"])
+    sp = to_np(plan.export("slot_pos"))
+    assert sp.view(np.uint32).tobytes() == B["slot_pos"].view(np.uint32).tobytes()
+    np.testing.assert_array_equal(to_np(plan.export("slot_idx")), B["slot_idx"])
+    meta = to_np(plan.export("chunk_meta"))
+    np.testing.assert_array_equal(meta[:, :3], B["chunk_anchor"])
+    np.testing.assert_array_equal(meta[:, 3], B["chunk_vol"])
+    lo = to_np(plan.export("chunk_lo"))
+    hi = to_np(plan.export("chunk_hi"))
+    np.testing.assert_array_equal(lo[:, :3].view(np.uint32), B["chunk_lo"].view(np.uint32))
+    np.testing.assert_array_equal(hi[:, :3].view(np.uint32), B["chunk_hi"].view(np.uint32))
+    np.testing.assert_array_equal(lo[:, 3].view(np.int32), B["chunk_count"])
+
+
+@pytest.mark.parametrize("name", ["uniform4k", "zeldovich128", "clustered256", "batch64"])
+def test_bin_bit_exact_small(name):
+    cfg = wc.small_variant(name)
+    w = wc.make_workload(cfg)
+    plan = _run_bin(w["volumes"], w["params"])
+    _compare(plan, w["volumes"])
+
+
+@pytest.mark.parametrize("sub_bits,n_cells", [(1, 0), (4, 3), (8, 5)])
+def test_bin_geometry_variants(sub_bits, n_cells):
+    pos = gen.uniform_box(3000, 17.0, 21)            # h not a power of two
+    vols = [(pos, 17.0)]
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), sub_bits=sub_bits, n_cells=[n_cells])
+    _compare(plan, vols)
+
+
+def test_bin_edge_positions():
+    L = 16.0
+    pos = gen.uniform_box(500, L, 3)
+    pos[:6] = [[0, 0, 0], [L - 1e-13, L - 1e-13, L - 1e-13], [-1e-300, 5, 5],
+               [-L, 2 * L - 1e-9, 3.0], [L, 0.5, 0.5], [4.0, 4.0, 4.0]]
+    pos[6:40] = pos[5]                               # duplicates: stable tie order
+    vols = [(pos, L)]
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8))
+    _compare(plan, vols)
+    plan.status()
+
+
+def test_bin_flags_out_of_range():
+    from paper_1411_3396_b300 import SrError
+    L = 16.0
+    pos = gen.uniform_box(100, L, 4)
+    pos[7, 1] = 2 * L + 1.0
+    pos[9, 2] = np.nan
+    plan = _run_bin([(pos, L)], dict(rc=3.0, eps=0.1, sigma=0.8))
+    with pytest.raises(SrError) as e:
+        plan.status()
+    assert e.value.code == 5
+    plan.status()                                    # flag cleared
+
+
+def test_bin_capacity_errors():
+    from paper_1411_3396_b300 import Plan, SrError
+    plan = Plan(16.0, 3.0, 0.1, 0.8, 100)
+    with pytest.raises(SrError) as e:
+        plan.bin(torch.zeros((101, 3), dtype=torch.float64, device="cuda"))
+    assert e.value.code == 3
+    with pytest.raises(SrError):
+        Plan(5.0, 3.0, 0.1, 0.8, 100)                # box <= 2 r_c
+    with pytest.raises(SrError):
+        Plan(16.0, 3.0, 0.0, 0.8, 100)               # eps must be > 0
+    with pytest.raises(SrError):
+        Plan(16.0, 3.0, 0.1, 0.8, 100, n_cells=6)    # cell side 2.67 < r_c
+
+
+def test_bin_partial_fill_and_rebin():
+    L = 16.0
+    plan = make_plan([(np.zeros((1, 3)), L)], dict(rc=3.0, eps=0.1, sigma=0.8))
+    from paper_1411_3396_b300 import Plan
+    plan = Plan(L, 3.0, 0.1, 0.8, 5000)
+    for seed, n in [(1, 5000), (2, 1234), (3, 1), (4, 4999)]:
+        pos = gen.uniform_box(n, L, seed)
+        plan.bin(torch.from_numpy(pos).cuda())
+        torch.cuda.synchronize()
+        _compare(plan, [(pos, L)])

@@ -1,0 +1,140 @@
+"""sr_force / sr_force_plain against the FP64 oracle: element-by-element
+forces within tolerance, bit-exact pair counts, determinism, invariants."""
+import numpy as np
+import pytest
+
+from oracle import binning as obin
+from oracle import fit as ofit
+from oracle import force as oforce
+from workloads import configs as wc
+from workloads import generators as gen
+
+from helpers import assert_force_close, make_plan, oracle_binning, oracle_force, rel_errors, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SMALL = ["uniform4k", "zeldovich128", "clustered256", "batch64", "diff64"]
+
+
+def _gpu(vols, params, count=True, **kw):
+    pos = np.concatenate([p for p, _ in vols])
+    plan = make_plan(vols, params, **kw)
+    plan.bin(torch.from_numpy(pos).cuda())
+    if count:
+        acc, pairs, pp = plan.force(count=True, per_particle=True)
+        torch.cuda.synchronize()
+        return plan, to_np(acc), int(pairs.item()), to_np(pp)
+    acc = plan.force()
+    torch.cuda.synchronize()
+    return plan, to_np(acc), None, None
+
+
+@pytest.fixture(scope="module", params=SMALL)
+def small_case(request):
+    cfg = wc.small_variant(request.param)
+    w = wc.make_workload(cfg)
+    return request.param, w
+
+
+def test_force_matches_oracle(small_case):
+    name, w = small_case
+    plan, acc, pairs, pp = _gpu(w["volumes"], w["params"])
+    a_ref, _ = oracle_force(w["volumes"], w["params"])
+    assert_force_close(acc, a_ref, name)
+    assert np.all(acc[:, 3] == 0)
+
+
+def test_force_matches_oracle_on_dequantised_positions(small_case):
+    # the kernel arithmetic alone (same binary32 inputs as the GPU)
+    name, w = small_case
+    plan, acc, _, _ = _gpu(w["volumes"], w["params"], count=False)
+    B = oracle_binning(plan, w["volumes"])
+    xr = obin.dequantized_positions(B, w["volumes"])
+    vols_r, k = [], 0
+    for pos, box in w["volumes"]:
+        vols_r.append((xr[k:k + len(pos)], box))
+        k += len(pos)
+    a_ref, _ = oracle_force(vols_r, w["params"])
+    rel = rel_errors(acc, a_ref)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4, (np.median(rel), rel.max())
+
+
+def test_pair_counts_bit_exact(small_case):
+    name, w = small_case
+    plan, acc, pairs, pp = _gpu(w["volumes"], w["params"])
+    B = oracle_binning(plan, w["volumes"])
+    ref = oforce.pair_counts_fp32(B, w["volumes"], w["params"]["rc"], w["params"]["eps"])
+    np.testing.assert_array_equal(pp, ref)
+    assert pairs == int(ref.sum())
+
+
+def test_counting_variant_gives_same_forces(small_case):
+    name, w = small_case
+    _, acc1, _, _ = _gpu(w["volumes"], w["params"], count=False)
+    _, acc2, _, _ = _gpu(w["volumes"], w["params"], count=True)
+    assert acc1.tobytes() == acc2.tobytes()
+
+
+def test_plain_kernel_matches_oracle(small_case):
+    name, w = small_case
+    pos = np.concatenate([p for p, _ in w["volumes"]])
+    plan = make_plan(w["volumes"], w["params"])
+    plan.bin(torch.from_numpy(pos).cuda())
+    acc = to_np(plan.force_plain())
+    a_ref, _ = oracle_force(w["volumes"], w["params"])
+    assert_force_close(acc, a_ref, name + " plain")
+
+
+def test_force_is_deterministic():
+    w = wc.make_workload(wc.small_variant("clustered256"))
+    pos = torch.from_numpy(np.concatenate([p for p, _ in w["volumes"]])).cuda()
+    plan = make_plan(w["volumes"], w["params"])
+    outs = []
+    for _ in range(3):
+        plan.bin(pos)
+        outs.append(to_np(plan.force()).tobytes())
+    assert outs[0] == outs[1] == outs[2]
+
+
+def test_force_brute_force_tiny_boxes():
+    for L, n, seed in [(7.0, 300, 1), (8.0, 512, 2), (10.0, 400, 3), (6.5, 64, 4)]:
+        pos = gen.uniform_box(n, L, seed)
+        params = dict(rc=3.0, eps=0.1, sigma=0.8)
+        _, acc, pairs, pp = _gpu([(pos, L)], params)
+        c = ofit.fit_poly(3.0, 0.8, 0.1)
+        a_ref, _ = oforce.accel_brute(pos, L, 3.0, 0.1, c)
+        assert_force_close(acc, a_ref, f"L={L}")
+
+
+def test_lattice_and_two_body():
+    params = dict(rc=3.0, eps=0.1, sigma=0.8)
+    pos = gen.lattice(12, 12.0)
+    _, acc, pairs, pp = _gpu([(pos, 12.0)], params)
+    assert np.max(np.abs(acc[:, :3])) < 1e-4           # binary32 of a zero sum
+    assert np.all(pp == pp[0])
+    c = ofit.fit_poly(3.0, 0.8, 0.1)
+    for r in (0.05, 0.7, 2.9):
+        pos = gen.two_body(r, 20.0, axis=2)
+        _, acc, pairs, pp = _gpu([(pos, 20.0)], params)
+        a_ref, _ = oforce.accel_brute(pos, 20.0, 3.0, 0.1, c)
+        # binary32 cancellation in r^-3 - p near r_c: absolute error relative to 1/r^2
+        np.testing.assert_allclose(acc[:, :3], a_ref, rtol=2e-6, atol=2e-6 / r ** 2)
+        assert pairs == 2
+
+
+def test_single_particle_and_far_pair():
+    params = dict(rc=3.0, eps=0.1, sigma=0.8)
+    _, acc, pairs, pp = _gpu([(np.array([[3.0, 4.0, 5.0]]), 16.0)], params)
+    assert np.all(acc == 0) and pairs == 0
+    _, acc, pairs, pp = _gpu([(np.array([[1.0, 1.0, 1.0], [9.0, 9.0, 9.0]]), 16.0)], params)
+    assert np.all(acc == 0) and pairs == 0
+
+
+def test_newton_third_law_on_gpu():
+    w = wc.make_workload(wc.small_variant("clustered256"))
+    plan, acc, _, _ = _gpu(w["volumes"], w["params"], count=False)
+    vel = torch.zeros((acc.shape[0], 4), dtype=torch.float32, device="cuda")
+    inv = to_np(plan.invariants(vel, torch.from_numpy(acc).cuda()))
+    assert np.all(np.abs(inv[3:6]) <= 1e-5 * np.abs(acc[:, :3]).sum())
