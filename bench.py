@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the short-range particle-particle step on B300.
+
+Metric: short-range pair interactions per second (binary32), i.e. ordered
+in-range pairs (i, j), i != j, counted bit-exactly by the library's
+binary32 predicate, divided by the time of one whole step.  A step is
+sr_bin (binning + stable counting sort + chunking + cost/order) ->
+sr_force (persistent pair kernel) -> sr_kick -> sr_invariants, through the
+C ABI, on inputs already resident in HBM.
+
+Default workload: the clustered 256^3 set (16,777,216 particles, half in
+NFW halos of 100..200,000 particles, half uniform, box 256, r_c = 3,
+eps = 0.05), seeded synthetic data.  Inputs exceed L2 (positions alone are
+402 MB), so no explicit L2 flush is done between steps.
+
+Also reported: the pair kernel against the binary32 ALU roofline
+(28 flops per in-range pair), the plain one-launch-per-slab kernel on the
+same input, an end-to-end step from pinned host buffers, SM clocks sampled
+during the timed region, and the FP64 oracle timed on a bounded sample on
+the host cores.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (no data-path collective); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_PAIR = 28          # 3 sub, 3 fma (s'), 1 mul + 1 fma (r^3 - q), 5 fma Horner, 3 fma accumulate
+FP32_LANES_PER_SM = 128
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "force_clustered256.md")
+
+_CPU_STATE = {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (fork pool created before any CUDA call)
+# ---------------------------------------------------------------------------
+
+def _cpu_rows(rows):
+    from oracle import force as oforce
+    st = _CPU_STATE
+    t0 = time.perf_counter()
+    _, cnt = oforce.accel_rows(st["pos"], st["box"], st["rc"], st["eps"], st["coef"], rows, tree=st["tree"])
+    return int(cnt.sum()), time.perf_counter() - t0
+
+
+def cpu_oracle_sample(pos, box, prm, n_rows, seed, cores, reps=1):
+    """Time the FP64 oracle's per-row force on n_rows random particles
+    (k-d tree built before timing).  Returns (pairs/s, pairs, seconds)."""
+    from scipy.spatial import cKDTree
+
+    from oracle import fit as ofit
+    wrapped = np.mod(pos, box)
+    wrapped[wrapped >= box] = 0.0
+    _CPU_STATE.update(pos=wrapped, box=box, rc=prm["rc"], eps=prm["eps"],
+                      coef=ofit.fit_poly(prm["rc"], prm["sigma"], prm["eps"]),
+                      tree=cKDTree(wrapped, boxsize=box))
+    rng = np.random.default_rng(seed)
+    results = []
+    ctx = mp.get_context("fork")
+    with ctx.Pool(cores) as pool:
+        for _ in range(reps):
+            rows = rng.choice(len(pos), n_rows, replace=False)
+            parts = np.array_split(rows, cores * 4)
+            t0 = time.perf_counter()
+            out = pool.map(_cpu_rows, parts)
+            el = time.perf_counter() - t0
+            results.append((sum(o[0] for o in out), el))
+    pairs = sum(r[0] for r in results)
+    secs = sum(r[1] for r in results)
+    return pairs / secs, pairs, secs, [r[0] / r[1] for r in results]
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for name in ("force.cu", "sr_internal.h"):
+        with open(os.path.join(ROOT, "paper_1411_3396_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, or None
+    if the summary is missing or was taken on a different kernel source."""
+    if not os.path.exists(PROFILE_NOTE):
+        return None
+    text = open(PROFILE_NOTE).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock, power and throttle reasons."""
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and self.uuid not in parts[1] and parts[1] not in self.uuid:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[2]), max=float(parts[3]),
+                                     power=float(parts[4]) if parts[4] not in ("[N/A]", "N/A") else 0.0,
+                                     hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 250.0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return dict(sm_mhz=float(np.median([r["sm"] for r in load])), sm_max_mhz=max(r["max"] for r in rows),
+                    reasons=sorted(reasons), samples=len(load))
+
+
+def make_inputs(name, n_particles=0):
+    from workloads import configs as wc
+    cfg = wc.resized(name, n_particles) if n_particles else wc.CONFIGS[name]
+    w = wc.make_workload(cfg)
+    if len(w["volumes"]) != 1:
+        raise SystemExit("bench.py times single-volume workloads (uniform4k, zeldovich128, clustered256, diff64)")
+    (pos, box), = w["volumes"]
+    return cfg, pos, box, w["velocities"], w["params"]
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    cfg, pos, box, vel, prm = make_inputs(args.workload, args.n_particles)
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    total = args.warmup + args.steps
+    rate, pairs, secs, per = cpu_oracle_sample(pos, box, prm, args.ref_rows, 7, cores, reps=total)
+    per = per[args.warmup:]
+    value = float(np.mean(per))
+    line = {
+        "impl": "reference", "metric": "short-range pair interactions/sec (FP32 path; oracle FP64)",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_particles": int(len(pos)), "box": box,
+                   "r_c": prm["rc"], "eps": prm["eps"], "sigma": prm["sigma"]},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.ref_rows} random rows per step (FP64 k-d tree row sums; tree build untimed)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    cfg, pos, box, vel_np, prm = make_inputs(args.workload, args.n_particles)
+    n = len(pos)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cores = os.cpu_count() or 1
+        rate, pairs, secs, _ = cpu_oracle_sample(pos, box, prm, args.cpu_rows, 11, cores)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_rows} random particles of the same workload, {pairs} pairs in {secs:.1f} s "
+                         "(FP64 k-d tree row sums, tree build untimed)"}
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1411_3396_b300 import Plan, kick, launch_count
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    x = torch.from_numpy(pos).to(dev)
+    vel = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+    vel[:, :3] = torch.from_numpy(vel_np).to(dev).float()
+    acc = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    inv = torch.empty(7, dtype=torch.float64, device=dev)
+    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n)
+    dt = prm["dt"]
+
+    def step(ev=None):
+        plan.bin(x)
+        if ev is not None:
+            ev[0].record()
+        plan.force(acc)
+        if ev is not None:
+            ev[1].record()
+        kick(acc, vel, dt)
+        plan.invariants(vel, acc, inv)
+
+    # pair count of this configuration (binary32 predicate, counting variant)
+    plan.bin(x)
+    _, pairs_t, _ = plan.force(acc, count=True)
+    torch.cuda.synchronize()
+    pairs = int(pairs_t.item())
+    info = plan.info()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    uuid = str(getattr(props, "uuid", "")) if hasattr(props, "uuid") else ""
+    sampler = ClockSampler(uuid if rank == 0 else "")
+    if rank == 0 and not args.no_clocks:
+        sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    t_start.record()
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    l1 = launch_count()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
+    ms = t_start.elapsed_time(t_end) / args.steps
+    force_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    plan.status()
+
+    ms_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_max = float(tt.item())
+    value = pairs * world / (ms_max * 1e-3)
+
+    # plain one-launch-per-slab kernel on the same binned input
+    plain = None
+    if not args.no_plain:
+        plan.bin(x)
+        plan.force_plain(acc)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.force_plain(acc)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        plain = {"ms": plain_ms, "pairs_per_s": pairs / (plain_ms * 1e-3),
+                 "speedup_of_persistent_kernel": plain_ms / force_ms}
+
+    # end to end: pinned host buffers, H2D + step + D2H inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(pos).pin_memory()
+        vel_h = vel.cpu().pin_memory()
+        acc_h = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+        plan.step_host(pos_h, vel_h, acc_h, dt)
+        ts = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            plan.step_host(pos_h, vel_h, acc_h, dt)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(ts))
+        e2e = {"value": pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(n * (24 + 16)),
+               "d2h_bytes_per_step": int(n * (16 + 16)), "ms_per_step": e2e_s * 1e3}
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = pairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12
+    traffic = recorded_traffic()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "short-range pair interactions/sec (FP32) and % of B300 FP32 peak vs plain kernel",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_particles": n, "box": box, "r_c": prm["rc"],
+                   "eps": prm["eps"], "sigma": prm["sigma"], "dt": dt, "pairs_per_step": pairs,
+                   "n_chunks": info["n_chunks"], "workers": info["workers"],
+                   "l2": "inputs larger than L2 (402 MB positions); no flush",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "k_pairs<force>", "kernel_ms": force_ms,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived, not measured)",
+                     "flops_per_pair": FLOPS_PER_PAIR},
+        "plain": plain,
+        "e2e": e2e,
+        "gpu_launches": int(l1 - l0),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="clustered256")
+    ap.add_argument("--n-particles", type=int, default=0,
+                    help="resize the workload (box scaled to keep density 1); 0 = as named")
+    ap.add_argument("--cpu-rows", type=int, default=2048)
+    ap.add_argument("--ref-rows", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

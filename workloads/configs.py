@@ -47,6 +47,18 @@ def small_variant(name: str) -> dict:
     return cfg
 
 
+def resized(name: str, n: int) -> dict:
+    """A workload with n particles and the box scaled to keep the mean
+    density of one particle per cell (box side round(n^(1/3)))."""
+    cfg = dict(CONFIGS[name])
+    side = float(round(n ** (1.0 / 3.0)))
+    if cfg["kind"] == "zeldovich":
+        cfg.update(n_side=int(side), box=side)
+    else:
+        cfg.update(n=int(n), box=side)
+    return cfg
+
+
 def make_workload(cfg: dict) -> dict:
     """Materialise a workload description.
 
