@@ -237,7 +237,8 @@ def run_ours(args, rank, world, local_rank):
     vel[:, :3] = torch.from_numpy(vel_np).to(dev).float()
     acc = torch.empty((n, 4), dtype=torch.float32, device=dev)
     inv = torch.empty(7, dtype=torch.float64, device=dev)
-    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n)
+    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n, n_cells=args.n_cells, sub_bits=args.sub_bits,
+                chunk_size=args.chunk_size)
     dt = prm["dt"]
 
     def step(ev=None):
@@ -252,10 +253,17 @@ def run_ours(args, rank, world, local_rank):
 
     # pair count of this configuration (binary32 predicate, counting variant)
     plan.bin(x)
+    tune_ms = None
+    if args.variant >= 0:
+        plan.set_variant(args.variant)
+    elif not args.no_autotune:
+        tune_ms = plan.autotune(reps=1)
     _, pairs_t, _ = plan.force(acc, count=True)
     torch.cuda.synchronize()
     pairs = int(pairs_t.item())
     info = plan.info()
+    ctr = plan.export("counters").cpu().numpy()
+    evals, lane_evals = int(ctr[3]), int(ctr[4])
 
     for _ in range(args.warmup):
         step()
@@ -339,6 +347,10 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "n_particles": n, "box": box, "r_c": prm["rc"],
                    "eps": prm["eps"], "sigma": prm["sigma"], "dt": dt, "pairs_per_step": pairs,
                    "n_chunks": info["n_chunks"], "workers": info["workers"],
+                   "variant": info["variant"], "autotune_ms": tune_ms, "chunk_size": info["chunk_size"],
+                   "sub_bits": info["sub_bits"], "n_cells": plan.volume(0)["n_cells"],
+                   "in_range_fraction": pairs / max(evals, 1),
+                   "lane_fill": evals / max(lane_evals, 1),
                    "l2": "inputs larger than L2 (402 MB positions); no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
@@ -372,6 +384,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1, help="force a pair-kernel variant (skips autotuning)")
+    ap.add_argument("--chunk-size", type=int, default=0, help="particles per chunk: 32 or 64 (0 = library default)")
+    ap.add_argument("--n-cells", type=int, default=0, help="cells per axis (0 = library default)")
+    ap.add_argument("--sub-bits", type=int, default=0, help="Morton bits per axis in a cell (0 = default)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -56,8 +56,8 @@ extern "C" {
 #define SR_EXPORT_PERM              0  /* int32[n]: sorted position -> caller index */
 #define SR_EXPORT_CELL_START        1  /* int32[total_cells+1]: first sorted position of each cell */
 #define SR_EXPORT_CELL_CHUNK_START  2  /* int32[total_cells+1]: first chunk of each cell */
-#define SR_EXPORT_SLOT_POS          3  /* float[4*32*n_chunks]: chunk-relative offsets (units of h) */
-#define SR_EXPORT_SLOT_IDX          4  /* int32[32*n_chunks]: caller index per slot, -1 = empty */
+#define SR_EXPORT_SLOT_POS          3  /* float[4*C*n_chunks]: chunk-relative offsets (units of h), C = chunk size */
+#define SR_EXPORT_SLOT_IDX          4  /* int32[C*n_chunks]: caller index per slot, -1 = empty */
 #define SR_EXPORT_CHUNK_META        5  /* int32[4*n_chunks]: anchor (qx, qy, qz) and volume */
 #define SR_EXPORT_CHUNK_LO          6  /* float[4*n_chunks]: bbox min (x,y,z), w = particle count (int bits) */
 #define SR_EXPORT_CHUNK_HI          7  /* float[4*n_chunks]: bbox max (x,y,z), w = 0 */
@@ -76,7 +76,7 @@ typedef struct sr_params {
     int    fit_mode;  /* SR_FIT_CONSTRAINED or SR_FIT_UNCONSTRAINED                    */
     int    n_cells;   /* cells per axis; 0 = automatic (side close to 4, >= r_c)        */
     int    sub_bits;  /* Morton bits per axis inside a cell (1..8); 0 = automatic (6)  */
-    int    reserved;  /* must be 0                                                     */
+    int    chunk_size;/* particles per chunk: 32 or 64; 0 = automatic (64)             */
 } sr_params;
 
 /* Read-only description of a plan (sizes of the exportable arrays). */
@@ -91,6 +91,8 @@ typedef struct sr_plan_info {
     int32_t key_bits;      /* significant bits of the sort key                         */
     int32_t workers;       /* resident warps of the persistent force kernel            */
     int32_t warps_per_block;
+    int32_t variant;       /* selected pair-kernel variant (see sr_plan_set_variant)   */
+    int32_t chunk_size;    /* particles per chunk (32 or 64)                           */
     double  coef[6];       /* fitted p(s) = sum_k coef[k] s^k (binary64)               */
 } sr_plan_info;
 
@@ -115,8 +117,9 @@ int sr_fit_poly(double r_c, double sigma, double eps, int mode, double c_out[6])
  * plus 8 bytes per cell) on the current device; no later call allocates.
  * Binning (Sec. 2.1 step 1, "partition into overlapping blocks"): cells of
  * side L/n_cells >= r_c; each cell's particles in Morton order of their
- * sub-cell (2^sub_bits per axis); chunks of <= 32 consecutive particles per
- * cell are the work units, each with a binary64 anchor and binary32 offsets.
+ * sub-cell (2^sub_bits per axis); chunks of <= chunk_size (32 or 64)
+ * consecutive particles per cell are the work units, each with a binary64
+ * anchor and binary32 offsets.
  * Errors: SR_ERR_ARG (bad parameters, n_max < 1 or > 2^30), SR_ERR_CUDA
  * (allocation failed).  *out is NULL on failure.
  */
@@ -125,8 +128,8 @@ int sr_plan_create(const sr_params* params, int64_t n_max, sr_plan** out);
 /*
  * sr_plan_batch -- plan for n_vol independent periodic volumes evaluated
  * together (one binning, one persistent force launch).  params[v].box and
- * n_cells may differ per volume; r_c, eps, sigma, fit_mode and sub_bits
- * must be equal.  n[v] (host array) is volume v's particle count; sr_bin
+ * n_cells may differ per volume; r_c, eps, sigma, fit_mode, sub_bits and
+ * chunk_size must be equal.  n[v] (host array) is volume v's particle count; sr_bin
  * then takes the concatenation, sum n[v] rows.
  * Errors: as sr_plan_create, plus SR_ERR_ARG for mismatched physics.
  */
@@ -254,6 +257,29 @@ int sr_plan_copy(sr_plan* plan, int which, void* dst, int64_t bytes, void* strea
  */
 int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float dt,
                  int64_t n, void* stream);
+
+/*
+ * sr_plan_set_variant -- select the pair-kernel variant used by sr_force
+ * (same arithmetic and summation order, different launch shape):
+ *   0..3: 256-thread blocks, at least 1, 2, 3, 4 resident per SM
+ *         (register budgets 255, 128, 85, 64 per thread);
+ *   4, 5: 128-thread blocks, at least 6, 7 per SM, split partial sums;
+ *   6, 7: 256-thread blocks, at least 3, 2 per SM, split partial sums.
+ * Split partial sums add even and odd neighbours of a 32-neighbour batch
+ * separately before the compensated update, so results differ from
+ * variants 0..3 in the last bits.  Errors: SR_ERR_ARG.
+ */
+int sr_plan_set_variant(sr_plan* plan, int variant);
+
+/*
+ * sr_autotune -- time each pair-kernel variant on the data of the last
+ * sr_bin (reps launches each, CUDA events on stream, synchronising) and
+ * keep the fastest.  acc: device float4 rows used as scratch output.
+ * ms_out: host float[8], nullable, receives the mean time per variant.
+ * This is a set-up call: it synchronises and must not be captured.
+ * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG, SR_ERR_CUDA.
+ */
+int sr_autotune(sr_plan* plan, float* acc, int reps, float* ms_out, void* stream);
 
 /* sr_last_error -- message of the last failure on this thread ("" if none). */
 const char* sr_last_error(void);

@@ -1,10 +1,10 @@
-"""Cell binning, sub-cell order and 32-particle chunks (bit-exact spec).
+"""Cell binning, sub-cell order and 32- or 64-particle chunks (bit-exact spec).
 
 This is the partition step of the paper's short-range timestep (Sec. 2.1,
 step 1: each node volume is partitioned into overlapping data blocks holding
 "active" particles, whose neighbours within the cutoff are read as "passive"
-ones).  Here the blocks are chunks of at most 32 spatially consecutive
-particles inside a cell; a chunk's passive set is every particle within r_c
+ones).  Here the blocks are chunks of at most C spatially consecutive
+particles inside a cell (32 or 64); a chunk's passive set is every particle within r_c
 of it, read from the neighbouring cells.
 
 Spec, per volume of side L with n_c cells per axis and b sub-cell bits:
@@ -18,9 +18,9 @@ Spec, per volume of side L with n_c cells per axis and b sub-cell bits:
 4. key:    (global cell id << 3b) | morton(sub), morton bit 3i = bit i of x,
            3i+1 of y, 3i+2 of z.  Particles are ordered by key, ties by the
            original index (a stable sort).
-5. chunks: each cell's run of n particles is cut into ceil(n / 32) chunks of
-           32 consecutive particles (last one ragged); chunk ids follow cell
-           order.  Chunk k owns slots [32k, 32k + 32).
+5. chunks: each cell's run of n particles is cut into ceil(n / C) chunks of
+           C consecutive particles (last one ragged; C = 32 or 64); chunk ids
+           follow cell order.  Chunk k owns slots [Ck, Ck + C).
 6. anchor: the fine-cell coordinates qA of the chunk's first particle; the
            chunk origin is qA * h (binary64).
 7. offset: per particle, off = binary32(t - qA) (the binary64 difference is
@@ -69,14 +69,15 @@ def fine_coords(x, box: float, n_c: int, b: int):
     return t, q
 
 
-def bin_particles(volumes, n_cells, sub_bits: int) -> dict:
+def bin_particles(volumes, n_cells, sub_bits: int, chunk: int = CHUNK) -> dict:
     """Bin a batch of volumes.
 
     volumes: list of (positions (n_v, 3) float64, L_v); n_cells: list of n_c
-    per volume.  Returns arrays in the sorted / chunked layout plus the
-    per-particle fine coordinates.
+    per volume; chunk: particles per chunk C.  Returns arrays in the sorted /
+    chunked layout plus the per-particle fine coordinates.
     """
     b = int(sub_bits)
+    C = int(chunk)
     ts, qs, cells, keys, vols = [], [], [], [], []
     base = 0
     for v, ((pos, box), n_c) in enumerate(zip(volumes, n_cells)):
@@ -98,24 +99,24 @@ def bin_particles(volumes, n_cells, sub_bits: int) -> dict:
     cell_s = cell[perm]
     cell_start = np.searchsorted(cell_s, np.arange(total_cells + 1), side="left")
     counts = np.diff(cell_start)
-    nch = (counts + CHUNK - 1) // CHUNK
+    nch = (counts + C - 1) // C
     cell_chunk_start = np.concatenate([[0], np.cumsum(nch)]).astype(np.int64)
     n_chunks = int(cell_chunk_start[-1])
 
     rank = np.arange(n) - cell_start[cell_s]
-    chunk_of = cell_chunk_start[cell_s] + rank // CHUNK
-    slot_of = chunk_of * CHUNK + rank % CHUNK
-    first = cell_start[cell_s] + (rank // CHUNK) * CHUNK
+    chunk_of = cell_chunk_start[cell_s] + rank // C
+    slot_of = chunk_of * C + rank % C
+    first = cell_start[cell_s] + (rank // C) * C
     q_s = q[perm]
     t_s = t[perm]
     qa = q_s[first]
     off = f32(t_s - qa)
 
-    slot_pos = np.zeros((n_chunks * CHUNK, 4), dtype=np.float32)
+    slot_pos = np.zeros((n_chunks * C, 4), dtype=np.float32)
     slot_pos[:, :3] = PAD
     slot_pos[slot_of, :3] = off
     slot_pos[slot_of, 3] = 1.0
-    slot_idx = np.full(n_chunks * CHUNK, -1, dtype=np.int64)
+    slot_idx = np.full(n_chunks * C, -1, dtype=np.int64)
     slot_idx[slot_of] = perm
 
     chunk_anchor = np.zeros((n_chunks, 3), dtype=np.int64)
@@ -134,7 +135,7 @@ def bin_particles(volumes, n_cells, sub_bits: int) -> dict:
     slot_orig = np.empty(n, dtype=np.int64)
     slot_orig[perm] = slot_of
     return dict(
-        n=n, sub_bits=b, n_cells=list(n_cells), total_cells=total_cells,
+        n=n, sub_bits=b, chunk=C, n_cells=list(n_cells), total_cells=total_cells,
         key_sorted=key_s, perm=perm, cell_start=cell_start,
         cell_chunk_start=cell_chunk_start, n_chunks=n_chunks,
         slot_pos=slot_pos, slot_idx=slot_idx, chunk_anchor=chunk_anchor,
@@ -150,7 +151,7 @@ def dequantized_positions(binned: dict, volumes) -> np.ndarray:
     n = binned["n"]
     out = np.empty((n, 3))
     slot = binned["slot_of"]
-    chunk = slot // CHUNK
+    chunk = slot // binned["chunk"]
     off = binned["slot_pos"][slot, :3].astype(np.float64)
     qa = binned["chunk_anchor"][chunk].astype(np.float64)
     vol = binned["chunk_vol"][chunk]

@@ -28,7 +28,6 @@ import numpy as np
 from scipy.spatial import cKDTree
 
 from . import fp32
-from .binning import CHUNK
 from .fit import f_sr
 
 
@@ -210,7 +209,7 @@ def pair_counts_fp32(binned, volumes, rc, eps, rows=None, margin=1e-3):
     """
     b = binned["sub_bits"]
     slot = binned["slot_of"]
-    chunk = slot // CHUNK
+    chunk = slot // binned["chunk"]
     off = binned["slot_pos"][slot, :3]
     qa = binned["chunk_anchor"][chunk]
     n_tot = binned["n"]

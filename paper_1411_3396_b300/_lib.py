@@ -16,7 +16,7 @@ EXPORTS = {
 
 class SrParams(ctypes.Structure):
     _fields_ = [("box", c_double), ("r_c", c_double), ("eps", c_double), ("sigma", c_double),
-                ("fit_mode", c_int), ("n_cells", c_int), ("sub_bits", c_int), ("reserved", c_int)]
+                ("fit_mode", c_int), ("n_cells", c_int), ("sub_bits", c_int), ("chunk_size", c_int)]
 
 
 class SrPlanInfo(ctypes.Structure):
@@ -24,6 +24,7 @@ class SrPlanInfo(ctypes.Structure):
                 ("total_cells", c_int64), ("max_chunks", c_int64), ("n_chunks", c_int64),
                 ("sub_bits", ctypes.c_int32), ("key_bits", ctypes.c_int32),
                 ("workers", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("chunk_size", ctypes.c_int32),
                 ("coef", c_double * 6)]
 
 
@@ -51,6 +52,8 @@ SIGNATURES = {
     "sr_plan_status": (c_int, [c_void_p, c_void_p]),
     "sr_plan_copy": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p]),
     "sr_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
+    "sr_plan_set_variant": (c_int, [c_void_p, c_int]),
+    "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
     "sr_last_error": (c_char_p, []),
     "sr_launch_count": (c_int64, []),
 }

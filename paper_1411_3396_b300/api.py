@@ -54,9 +54,9 @@ def kick(acc: torch.Tensor, vel: torch.Tensor, dt: float):
     return vel
 
 
-def _params(box, r_c, eps, sigma, fit_mode, n_cells, sub_bits):
+def _params(box, r_c, eps, sigma, fit_mode, n_cells, sub_bits, chunk_size):
     return SrParams(float(box), float(r_c), float(eps), float(sigma), FIT_MODES[fit_mode],
-                    int(n_cells), int(sub_bits), 0)
+                    int(n_cells), int(sub_bits), int(chunk_size))
 
 
 class Plan:
@@ -64,18 +64,18 @@ class Plan:
 
     def __init__(self, box: float, r_c: float, eps: float, sigma: float, n_max: int,
                  fit_mode: str = "constrained", n_cells: int = 0, sub_bits: int = 0,
-                 _batch=None):
+                 chunk_size: int = 0, _batch=None):
         lib = load()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         handle = c_void_p()
         if _batch is None:
-            prm = _params(box, r_c, eps, sigma, fit_mode, n_cells, sub_bits)
+            prm = _params(box, r_c, eps, sigma, fit_mode, n_cells, sub_bits, chunk_size)
             check(lib.sr_plan_create(byref(prm), int(n_max), byref(handle)))
             self.volume_counts = [int(n_max)]
         else:
             boxes, counts, cells = _batch
-            arr = (SrParams * len(boxes))(*[_params(b, r_c, eps, sigma, fit_mode, nc, sub_bits)
+            arr = (SrParams * len(boxes))(*[_params(b, r_c, eps, sigma, fit_mode, nc, sub_bits, chunk_size)
                                             for b, nc in zip(boxes, cells)])
             ns = (c_int64 * len(counts))(*[int(c) for c in counts])
             check(lib.sr_plan_batch(arr, ns, len(boxes), byref(handle)))
@@ -87,9 +87,9 @@ class Plan:
 
     @classmethod
     def batch(cls, boxes, counts, r_c, eps, sigma, fit_mode="constrained", n_cells=None,
-              sub_bits=0):
+              sub_bits=0, chunk_size=0):
         cells = n_cells if n_cells is not None else [0] * len(boxes)
-        return cls(0.0, r_c, eps, sigma, 0, fit_mode, 0, sub_bits, _batch=(boxes, counts, cells))
+        return cls(0.0, r_c, eps, sigma, 0, fit_mode, 0, sub_bits, chunk_size, _batch=(boxes, counts, cells))
 
     # -- lifecycle -----------------------------------------------------------
     def close(self):
@@ -173,6 +173,18 @@ class Plan:
         check(load().sr_invariants(self._h, n, _ptr(vel), _ptr(acc), _ptr(out), _stream()))
         return out
 
+    def set_variant(self, v: int):
+        check(load().sr_plan_set_variant(self._h, int(v)))
+
+    def autotune(self, reps: int = 2):
+        """Time the pair-kernel variants on the current binning; keeps the
+        fastest and returns the per-variant mean times (ms)."""
+        n = self._need_binned()
+        acc = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        ms = (ctypes.c_float * 8)()
+        check(load().sr_autotune(self._h, _ptr(acc), int(reps), ms, _stream()))
+        return list(ms)
+
     def status(self):
         check(load().sr_plan_status(self._h, _stream()))
 
@@ -183,7 +195,8 @@ class Plan:
         spec = {
             "perm": (torch.int32, (n,)), "cell_start": (torch.int32, (cells + 1,)),
             "cell_chunk_start": (torch.int32, (cells + 1,)),
-            "slot_pos": (torch.float32, (nch * 32, 4)), "slot_idx": (torch.int32, (nch * 32,)),
+            "slot_pos": (torch.float32, (nch * inf["chunk_size"], 4)),
+            "slot_idx": (torch.int32, (nch * inf["chunk_size"],)),
             "chunk_meta": (torch.int32, (nch, 4)), "chunk_lo": (torch.float32, (nch, 4)),
             "chunk_hi": (torch.float32, (nch, 4)), "order": (torch.int32, (nch,)),
             "cost": (torch.int32, (nch,)), "counters": (torch.int64, (8,)),

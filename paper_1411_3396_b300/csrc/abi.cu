@@ -11,6 +11,8 @@
 namespace sr {
 namespace {
 thread_local std::string g_last_error;
+
+int variant_warps(int v) { return (v == 4 || v == 5) ? 4 : 8; }
 std::atomic<long long> g_launches{0};
 
 constexpr double kSideMargin = 1.0 + 1.0 / (1 << 20);   // cell side must exceed r_c by this factor
@@ -39,6 +41,7 @@ void free_plan(sr_plan* p) {
     cudaFree(p->cell_start);
     cudaFree(p->cell_nch);
     cudaFree(p->ccs);
+    cudaFree(p->chunk_cell);
     cudaFree(p->chunk_meta);
     cudaFree(p->chunk_lo);
     cudaFree(p->chunk_hi);
@@ -63,7 +66,8 @@ int check_physics(const sr_params& q) {
     if (!(q.sigma > 0) || !std::isfinite(q.sigma)) return set_error(SR_ERR_ARG, "sigma must be positive and finite");
     if (q.fit_mode != SR_FIT_CONSTRAINED && q.fit_mode != SR_FIT_UNCONSTRAINED)
         return set_error(SR_ERR_ARG, "bad fit_mode");
-    if (q.reserved != 0) return set_error(SR_ERR_ARG, "reserved must be 0");
+    if (q.chunk_size != 0 && q.chunk_size != 32 && q.chunk_size != 64)
+        return set_error(SR_ERR_ARG, "chunk_size must be 0, 32 or 64");
     if (q.sub_bits < 0 || q.sub_bits > 8) return set_error(SR_ERR_ARG, "sub_bits must be in 0..8");
     return SR_OK;
 }
@@ -90,6 +94,9 @@ int make_volume(const sr_params& q, const double coef[6], int b, int cell_base, 
     V->cell_base = cell_base;
     const double h = q.box / V->M;
     V->h = h;
+    int ex = 0;
+    V->h_pow2 = (std::frexp(h, &ex) == 0.5) ? 1 : 0;
+    V->inv_h = V->h_pow2 ? 1.0 / h : 0.0;
     const double h2 = h * h;
     const double e64 = q.eps * q.eps;
     V->eps2u = (float)(e64 / h2);
@@ -126,8 +133,9 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
         const sr_params& q = params[v];
         if ((rc = check_physics(q))) return rc;
         if (q.r_c != params[0].r_c || q.eps != params[0].eps || q.sigma != params[0].sigma ||
-            q.fit_mode != params[0].fit_mode || q.sub_bits != params[0].sub_bits)
-            return set_error(SR_ERR_ARG, "batch volumes must share r_c, eps, sigma, fit_mode, sub_bits");
+            q.fit_mode != params[0].fit_mode || q.sub_bits != params[0].sub_bits ||
+            q.chunk_size != params[0].chunk_size)
+            return set_error(SR_ERR_ARG, "batch volumes must share r_c, eps, sigma, fit_mode, sub_bits, chunk_size");
     }
     long long cap = 0;
     for (int v = 0; v < n_vol; ++v) {
@@ -141,6 +149,8 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
     p->n_vol = n_vol;
     p->capacity = cap;
     p->sub_bits = params[0].sub_bits ? params[0].sub_bits : 6;
+    p->chunk_k = params[0].chunk_size == 32 ? 1 : 2;
+    const long long C = 32 * p->chunk_k;
     if ((rc = fit_poly(params[0].r_c, params[0].sigma, params[0].eps, params[0].fit_mode, p->coef))) {
         delete p;
         return rc;
@@ -168,8 +178,8 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
     int cell_bits = 0;
     while ((1ll << cell_bits) < cells) ++cell_bits;
     p->key_bits = cell_bits + 3 * p->sub_bits;
-    p->max_chunks = (cap + kChunk - 1) / kChunk + (cap < cells ? cap : cells);
-    if (p->max_chunks * kChunk >= (1ll << 31)) { delete p; return set_error(SR_ERR_CAPACITY, "too many slots"); }
+    p->max_chunks = (cap + C - 1) / C + (cap < cells ? cap : cells);
+    if (p->max_chunks * C >= (1ll << 31)) { delete p; return set_error(SR_ERR_CAPACITY, "too many slots"); }
 
     cudaError_t ge = cudaGetDevice(&p->device);
     if (ge == cudaSuccess) ge = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
@@ -177,7 +187,7 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
         delete p;
         return cuda_fail(ge, "device query");
     }
-    const long long mc = p->max_chunks, slots = mc * kChunk;
+    const long long mc = p->max_chunks, slots = mc * C;
 #define SR_ALLOC(ptr, cnt)                                 \
     do {                                                   \
         if ((rc = dalloc(&(ptr), (size_t)(cnt)))) {        \
@@ -197,6 +207,7 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
     SR_ALLOC(p->cell_start, cells + 1);
     SR_ALLOC(p->cell_nch, cells + 1);
     SR_ALLOC(p->ccs, cells + 1);
+    SR_ALLOC(p->chunk_cell, mc);
     SR_ALLOC(p->chunk_meta, mc);
     SR_ALLOC(p->chunk_lo, mc);
     SR_ALLOC(p->chunk_hi, mc);
@@ -294,6 +305,10 @@ int sr_plan_get_info(sr_plan* p, sr_plan_info* info) {
     info->key_bits = p->key_bits;
     info->workers = p->force_blocks * p->warps_per_block;
     info->warps_per_block = p->warps_per_block;
+    info->variant = p->variant;
+    info->chunk_size = 32 * p->chunk_k;
+    info->warps_per_block = variant_warps(p->variant);
+    info->workers = p->force_blocks_v[p->variant] * info->warps_per_block;
     for (int k = 0; k < 6; ++k) info->coef[k] = p->coef[k];
     return SR_OK;
 }
@@ -382,13 +397,13 @@ int sr_plan_copy(sr_plan* p, int which, void* dst, int64_t bytes, void* stream) 
     if (!p || !dst || bytes < 0) return set_error(SR_ERR_ARG, "null argument");
     const void* src = nullptr;
     long long avail = 0;
-    const long long mc = p->max_chunks, cells = p->total_cells;
+    const long long mc = p->max_chunks, cells = p->total_cells, C = 32 * p->chunk_k;
     switch (which) {
         case SR_EXPORT_PERM: src = p->vals[p->sorted]; avail = 4 * p->capacity; break;
         case SR_EXPORT_CELL_START: src = p->cell_start; avail = 4 * (cells + 1); break;
         case SR_EXPORT_CELL_CHUNK_START: src = p->ccs; avail = 4 * (cells + 1); break;
-        case SR_EXPORT_SLOT_POS: src = p->slot_pos; avail = 16 * mc * kChunk; break;
-        case SR_EXPORT_SLOT_IDX: src = p->slot_idx; avail = 4 * mc * kChunk; break;
+        case SR_EXPORT_SLOT_POS: src = p->slot_pos; avail = 16 * mc * C; break;
+        case SR_EXPORT_SLOT_IDX: src = p->slot_idx; avail = 4 * mc * C; break;
         case SR_EXPORT_CHUNK_META: src = p->chunk_meta; avail = 16 * mc; break;
         case SR_EXPORT_CHUNK_LO: src = p->chunk_lo; avail = 16 * mc; break;
         case SR_EXPORT_CHUNK_HI: src = p->chunk_hi; avail = 16 * mc; break;
@@ -423,6 +438,45 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
     if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
     SR_CUDA_CHECK(cudaStreamSynchronize(st));
     return SR_OK;
+}
+
+int sr_plan_set_variant(sr_plan* p, int variant) {
+    if (!p || variant < 0 || variant >= kVariants) return set_error(SR_ERR_ARG, "variant out of range");
+    p->variant = variant;
+    p->force_blocks = p->force_blocks_v[variant];
+    return SR_OK;
+}
+
+int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->binned) return set_error(SR_ERR_STATE, "sr_autotune before sr_bin");
+    if (!acc || reps < 1) return set_error(SR_ERR_ARG, "acc is null or reps < 1");
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    SR_CUDA_CHECK(cudaEventCreate(&e0));
+    SR_CUDA_CHECK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = p->variant;
+    int rc = SR_OK;
+    for (int v = 0; v < kVariants && rc == SR_OK; ++v) {
+        p->variant = v;
+        if ((rc = launch_force(p, acc, nullptr, nullptr, st))) break;   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rc == SR_OK; ++r) rc = launch_force(p, acc, nullptr, nullptr, st);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "sr_autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->variant = best_v;
+    p->force_blocks = p->force_blocks_v[best_v];
+    return rc;
 }
 
 const char* sr_last_error(void) { return g_last_error.c_str(); }

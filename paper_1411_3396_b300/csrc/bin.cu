@@ -48,15 +48,17 @@ __device__ __forceinline__ int volume_of_cell(int cell, const int* __restrict__ 
 }
 
 // Fine-grid coordinate of one axis; flags non-finite / out-of-range input.
-__device__ __forceinline__ void fine_axis(double x, double box, double h, int M, double& t, int& q,
-                                          bool& bad) {
+__device__ __forceinline__ void fine_axis(double x, const VolDev& V, double& t, int& q, bool& bad) {
+    const double box = V.box;
+    const int M = V.M;
     if (!(x >= -box && x < 2.0 * box)) {  // also catches NaN
         bad = true;
         x = 0.0;
     }
     if (x < 0.0) x = x + box;
     if (x >= box) x = x - box;
-    t = x / h;
+    // x / h, correctly rounded; for h = 2^k the product with 2^-k is exact
+    t = V.h_pow2 ? x * V.inv_h : x / V.h;
     int qq = (int)floor(t);
     if (qq > M - 1) qq = M - 1;
     if (qq < 0) qq = 0;
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, in
     int q[3];
     double t[3];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) fine_axis(pos[3ll * i + ax], V.box, V.h, V.M, t[ax], q[ax], bad);
+    for (int ax = 0; ax < 3; ++ax) fine_axis(pos[3ll * i + ax], V, t[ax], q[ax], bad);
     const int mask = (1 << b) - 1;
     const int cell = V.cell_base + ((q[2] >> b) * V.n_c + (q[1] >> b)) * V.n_c + (q[0] >> b);
     const unsigned long long m = spread3(q[0] & mask) | (spread3(q[1] & mask) << 1) |
@@ -96,52 +98,78 @@ __global__ void __launch_bounds__(256) k_cell_bounds(const unsigned long long* _
 }
 
 __global__ void __launch_bounds__(256) k_cell_nch(const int* __restrict__ cell_start, int total_cells,
-                                                  int* __restrict__ nch) {
+                                                  int chunk, int* __restrict__ nch) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c > total_cells) return;
-    nch[c] = c < total_cells ? (cell_start[c + 1] - cell_start[c] + kChunk - 1) / kChunk : 0;
+    nch[c] = c < total_cells ? (cell_start[c + 1] - cell_start[c] + chunk - 1) / chunk : 0;
 }
 
-// One warp per chunk: slot positions / indices, anchor, bounding box.
+// chunk -> cell map: thread per cell writes its chunk range.
+__global__ void __launch_bounds__(256) k_chunk_cell(const int* __restrict__ ccs, int total_cells,
+                                                    int* __restrict__ chunk_cell) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= total_cells) return;
+    for (int k = ccs[c]; k < ccs[c + 1]; ++k) chunk_cell[k] = c;
+}
+
+// One warp per chunk of C = 32 K slots (lane l fills slots l + 32 s):
+// slot positions / indices, anchor, bounding box.
+template <int K>
 __global__ void __launch_bounds__(256) k_chunk_fill(
     const double* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ cell_start,
-    const int* __restrict__ ccs, int total_cells, const VolDev* __restrict__ vols,
-    const int* __restrict__ vol_cell_base, int n_vol, int b, float4* __restrict__ slot_pos,
-    int* __restrict__ slot_idx, int4* __restrict__ chunk_meta, float4* __restrict__ chunk_lo,
-    float4* __restrict__ chunk_hi) {
+    const int* __restrict__ ccs, const int* __restrict__ chunk_cell, int total_cells,
+    const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base, int n_vol,
+    float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
+    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi) {
+    constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
     const int n_chunks = ccs[total_cells];
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_chunks; k += warps) {
-        int lo = 0, hi = total_cells;              // ccs[lo] <= k < ccs[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (ccs[mid] <= k) lo = mid; else hi = mid;
-        }
-        const int cell = lo;
-        const int r0 = (k - ccs[cell]) * kChunk;
+        const int cell = chunk_cell[k];
+        const int r0 = (k - ccs[cell]) * C;
         const int n_cell = cell_start[cell + 1] - cell_start[cell];
-        const int rank = r0 + lane;
-        const bool valid = rank < n_cell;
         const int v = n_vol > 1 ? volume_of_cell(cell, vol_cell_base, n_vol) : 0;
         const VolDev& V = vols[v];
-        int orig = -1;
-        int q[3] = {0, 0, 0};
-        double t[3] = {0.0, 0.0, 0.0};
-        if (valid) {
-            orig = perm[cell_start[cell] + rank];
-            bool bad = false;
+        int orig[K], q[K][3];
+        double t[K][3];
+        bool valid[K];
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) fine_axis(pos[3ll * orig + ax], V.box, V.h, V.M, t[ax], q[ax], bad);
+        for (int s = 0; s < K; ++s) {
+            const int rank = r0 + lane + 32 * s;
+            valid[s] = rank < n_cell;
+            orig[s] = -1;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) { q[s][ax] = 0; t[s][ax] = 0.0; }
+            if (valid[s]) {
+                orig[s] = perm[cell_start[cell] + rank];
+                bool bad = false;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) fine_axis(pos[3ll * orig[s] + ax], V, t[s][ax], q[s][ax], bad);
+            }
         }
         int qa[3];
-        float off[3], bl[3], bh[3];
+        float bl[3], bh[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            qa[ax] = __shfl_sync(kFull, q[ax], 0);
-            off[ax] = valid ? __double2float_rn(t[ax] - (double)qa[ax]) : kPad;
-            bl[ax] = valid ? off[ax] : __int_as_float(0x7f800000);   // +inf
-            bh[ax] = valid ? off[ax] : __int_as_float(0xff800000);   // -inf
+            qa[ax] = __shfl_sync(kFull, q[0][ax], 0);      // slot 0 (rank r0) always exists
+            bl[ax] = __int_as_float(0x7f800000);          // +inf
+            bh[ax] = __int_as_float(0xff800000);          // -inf
+        }
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            float off[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                off[ax] = valid[s] ? __double2float_rn(t[s][ax] - (double)qa[ax]) : kPad;
+                if (valid[s]) {
+                    bl[ax] = fminf(bl[ax], off[ax]);
+                    bh[ax] = fmaxf(bh[ax], off[ax]);
+                }
+            }
+            const long long slot = (long long)k * C + lane + 32 * s;
+            slot_pos[slot] = make_float4(off[0], off[1], off[2], valid[s] ? 1.0f : 0.0f);
+            slot_idx[slot] = orig[s];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -151,11 +179,8 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
                 bh[ax] = fmaxf(bh[ax], __shfl_xor_sync(kFull, bh[ax], o));
             }
         }
-        const long long slot = (long long)k * kChunk + lane;
-        slot_pos[slot] = make_float4(off[0], off[1], off[2], valid ? 1.0f : 0.0f);
-        slot_idx[slot] = orig;
         if (lane == 0) {
-            const int cnt = min(kChunk, n_cell - r0);
+            const int cnt = min(C, n_cell - r0);
             chunk_meta[k] = make_int4(qa[0], qa[1], qa[2], v);
             chunk_lo[k] = make_float4(bl[0], bl[1], bl[2], __int_as_float(cnt));
             chunk_hi[k] = make_float4(bh[0], bh[1], bh[2], 0.0f);
@@ -180,16 +205,23 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st) {
     const int tc = (int)p->total_cells;
     k_cell_bounds<<<(ni + 1 + 255) / 256, 256, 0, st>>>(p->keys[which], ni, 3 * b, tc, p->cell_start);
     SR_LAUNCH_CHECK("k_cell_bounds");
-    k_cell_nch<<<(tc + 1 + 255) / 256, 256, 0, st>>>(p->cell_start, tc, p->cell_nch);
+    k_cell_nch<<<(tc + 1 + 255) / 256, 256, 0, st>>>(p->cell_start, tc, 32 * p->chunk_k, p->cell_nch);
     SR_LAUNCH_CHECK("k_cell_nch");
     rc = exclusive_scan(p->cell_nch, p->ccs, tc + 1, p->scan_cells, st);
     if (rc) return rc;
+    k_chunk_cell<<<(tc + 255) / 256, 256, 0, st>>>(p->ccs, tc, p->chunk_cell);
+    SR_LAUNCH_CHECK("k_chunk_cell");
     long long want = (p->max_chunks + 7) / 8;
     long long cap = (long long)p->sm_count * 16;
     const int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    k_chunk_fill<<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, tc, p->vols,
-                                         p->vol_cell_base, p->n_vol, b, p->slot_pos, p->slot_idx,
-                                         p->chunk_meta, p->chunk_lo, p->chunk_hi);
+    if (p->chunk_k == 2)
+        k_chunk_fill<2><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
+                                                p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
+                                                p->chunk_meta, p->chunk_lo, p->chunk_hi);
+    else
+        k_chunk_fill<1><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
+                                                p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
+                                                p->chunk_meta, p->chunk_lo, p->chunk_hi);
     SR_LAUNCH_CHECK("k_chunk_fill");
     return launch_cost_and_order(p, st);
 }

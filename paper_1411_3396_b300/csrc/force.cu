@@ -1,15 +1,16 @@
 // Short-range pair kernels: cost estimate + longest-first order, the
 // persistent force kernel and its vector-Jacobian product.
 //
-// Work decomposition (Sec. 2.1): every chunk (<= 32 particles of one cell)
-// is an "active" block; its "passive" particles are all particles within
-// r_c, read from the 27 neighbouring cells (periodic images included).
-// Only active particles are written (the reconcile step is implicit).
-// Load balance follows the same section: per-block cost estimates, and the
-// largest blocks are handed out first (longest-processing-time order) to
-// a fixed pool of workers -- one warp each -- pulling from an atomic queue.
+// Work decomposition (Sec. 2.1): every chunk (C = 32 K particles of one
+// cell, K = 1 or 2) is an "active" block; its "passive" particles are all
+// particles within r_c, read from the 27 neighbouring cells (periodic
+// images included).  Only active particles are written (the reconcile step
+// is implicit).  Load balance follows the same section: per-block cost
+// estimates, and the largest blocks are handed out first (longest-
+// processing-time order) to a fixed pool of workers -- one warp each --
+// pulling from an atomic queue.
 //
-// Per work item (one warp, lane = one active particle):
+// Per work item (one warp, lane l owns active slots l, l+32, ..., K of them):
 //   1. cell culling   : neighbour cells only where the chunk's box comes
 //                       within r_c of the cell wall;
 //   2. chunk culling  : 32 candidate chunks at a time, one per lane, by
@@ -19,9 +20,10 @@
 //                       box; survivors are compacted into a per-warp ring
 //                       in shared memory;
 //   4. pair loop      : every full batch of 32 ring entries is broadcast
-//                       from shared memory to all lanes; each lane sums
-//                       d f(s) over the batch in binary32 and adds the batch
-//                       partial into a Kahan-compensated accumulator.
+//                       from shared memory to all lanes; each entry meets
+//                       the lane's K particles; each lane sums d f(s) over
+//                       the batch in binary32 and adds the batch partial
+//                       into a Kahan-compensated accumulator.
 //
 // Units: offsets are in units of the fine grid h; shifts between chunks are
 // exact integers (anchor differences plus image multiples of M).  With
@@ -41,6 +43,7 @@ enum Mode { kForce = 0, kForceCount = 1, kVjp = 2 };
 
 struct Args {
     const int* ccs;
+    const int* cell_start;
     int total_cells;
     const int4* meta;
     const float4* clo;
@@ -61,6 +64,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// 1/sqrt(x) as one MUFU operation.  The argument s' = |d|^2 + eps^2/h^2 is
+// always a normal binary32 number (>= eps^2/h^2 > 0), so the flush-to-zero
+// variant gives the same value as the denormal-safe library routine.
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// (px, py, pz) += f * (dx, dy, dz) only where s < rc2: one compare and three
+// predicated FMAs (no select instructions).
+__device__ __forceinline__ void masked_axpy3(float s, float rc2, float f, float dx, float dy, float dz,
+                                             float& px, float& py, float& pz) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.lt.f32 p, %3, %4;\n\t"
+        "@p fma.rn.f32 %0, %5, %6, %0;\n\t"
+        "@p fma.rn.f32 %1, %5, %7, %1;\n\t"
+        "@p fma.rn.f32 %2, %5, %8, %2;\n\t}"
+        : "+f"(px), "+f"(py), "+f"(pz)
+        : "f"(s), "f"(rc2), "f"(f), "f"(dx), "f"(dy), "f"(dz));
 }
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
@@ -90,24 +115,34 @@ __device__ __forceinline__ Item load_item(const Args& a, int I) {
     return it;
 }
 
-// Calls visit(J, Sx, Sy, Sz, cntJ) for every chunk J whose box comes within
-// the culling radius of the item's box, in a fixed order (cells z, y, x
-// ascending offsets; chunks ascending).  Warp-uniform control flow.
-template <class Visit>
-__device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const Item& it, const VolDev& V,
-                                                         Visit&& visit) {
-    const int lane = threadIdx.x & 31;
+// Neighbour-cell offsets the chunk's box reaches: -1 if the box comes within
+// the culling radius of the lower wall, +1 of the upper wall.
+__device__ __forceinline__ void cell_range(const Item& it, const VolDev& V, int c[3], int olo[3], int ohi[3]) {
     const int b = V.sub_bits;
-    const int side = 1 << b;
-    int c[3], olo[3], ohi[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         c[ax] = it.q[ax] >> b;
         const float wall_lo = (float)((c[ax] << b) - it.q[ax]);
-        const float wall_hi = wall_lo + (float)side;
+        const float wall_hi = wall_lo + (float)(1 << b);
         olo[ax] = (it.lo[ax] - V.rcm < wall_lo) ? -1 : 0;
         ohi[ax] = (it.hi[ax] + V.rcm > wall_hi) ? 1 : 0;
     }
+}
+
+// Calls visit(J, Sx, Sy, Sz, pj, gj) for every chunk J whose box comes
+// within the culling radius of the item's box, in a fixed order (cells z, y,
+// x ascending offsets; chunks ascending); pj[k] / gj[k] are the lane's slots
+// lane + 32 k of chunk J (positions, and cotangents when WITH_G).
+// Warp-uniform control flow.  (Holding the next group's records in
+// registers to hide load latency was measured slower: it raises register
+// pressure across the pair batches.)
+template <int K, bool WITH_G, class Visit>
+__device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const Item& it, const VolDev& V,
+                                                         Visit&& visit) {
+    constexpr int C = 32 * K;
+    const int lane = threadIdx.x & 31;
+    int c[3], olo[3], ohi[3];
+    cell_range(it, V, c, olo, ohi);
     for (int oz = olo[2]; oz <= ohi[2]; ++oz) {
         int nz = c[2] + oz, kz = 0;
         if (nz < 0) { nz += V.n_c; kz = -1; } else if (nz >= V.n_c) { nz -= V.n_c; kz = 1; }
@@ -126,7 +161,6 @@ __device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const It
                     const int J = jb + lane;
                     bool pass = false;
                     float Sx = 0.f, Sy = 0.f, Sz = 0.f;
-                    int cj = 0;
                     if (J < j1) {
                         const int4 mj = a.meta[J];
                         const float4 lj = a.clo[J];
@@ -134,7 +168,6 @@ __device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const It
                         Sx = (float)(mj.x + bx);
                         Sy = (float)(mj.y + by);
                         Sz = (float)(mj.z + bz);
-                        cj = __float_as_int(lj.w);
                         const float gx = fmaxf(fmaxf(lj.x + Sx - it.hi[0], it.lo[0] - (hj.x + Sx)), 0.f);
                         const float gy = fmaxf(fmaxf(lj.y + Sy - it.hi[1], it.lo[1] - (hj.y + Sy)), 0.f);
                         const float gz = fmaxf(fmaxf(lj.z + Sz - it.hi[2], it.lo[2] - (hj.z + Sz)), 0.f);
@@ -144,8 +177,15 @@ __device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const It
                     while (mask) {
                         const int l = __ffs(mask) - 1;
                         mask &= mask - 1;
+                        float4 pj[K], gj[K];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const long long js = (long long)(jb + l) * C + lane + 32 * k;
+                            pj[k] = a.slot_pos[js];
+                            if (WITH_G) gj[k] = a.slot_g[js];
+                        }
                         visit(jb + l, __shfl_sync(kFull, Sx, l), __shfl_sync(kFull, Sy, l),
-                              __shfl_sync(kFull, Sz, l), __shfl_sync(kFull, cj, l));
+                              __shfl_sync(kFull, Sz, l), pj, gj);
                     }
                 }
             }
@@ -168,8 +208,7 @@ __device__ __forceinline__ Consts load_consts(const VolDev& V, bool vjp) {
     return k;
 }
 
-// Force on one lane's particle from one ring entry (x, y, z already in the
-// active chunk's frame).
+// Force on one particle from one ring entry (already in the active chunk's frame).
 template <bool COUNT>
 __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, float zi, const Consts& K,
                                            float& px, float& py, float& pz, int& npair) {
@@ -179,16 +218,12 @@ __device__ __forceinline__ void pair_force(const float4 q, float xi, float yi, f
     float s = fmaf(dx, dx, K.eps2);
     s = fmaf(dy, dy, s);
     s = fmaf(dz, dz, s);
-    const float r = rsqrtf(s);
+    const float r = rsqrt_mufu(s);
     const float r2 = r * r;
     const float nq = fmaf(fmaf(fmaf(fmaf(fmaf(K.n5, s, K.n4), s, K.n3), s, K.n2), s, K.n1), s, K.n0);
     const float f = fmaf(r2, r, nq);
-    if (s < K.rc2) {
-        px = fmaf(f, dx, px);
-        py = fmaf(f, dy, py);
-        pz = fmaf(f, dz, pz);
-        if (COUNT) ++npair;
-    }
+    masked_axpy3(s, K.rc2, f, dx, dy, dz, px, py, pz);
+    if (COUNT) npair += (s < K.rc2) ? 1 : 0;
 }
 
 __device__ __forceinline__ void pair_vjp(const float4 q, const float4 gj, float xi, float yi, float zi,
@@ -200,7 +235,7 @@ __device__ __forceinline__ void pair_vjp(const float4 q, const float4 gj, float 
     float s = fmaf(dx, dx, K.eps2);
     s = fmaf(dy, dy, s);
     s = fmaf(dz, dz, s);
-    const float r = rsqrtf(s);
+    const float r = rsqrt_mufu(s);
     const float r2 = r * r;
     const float r3 = r2 * r;
     const float nq = fmaf(fmaf(fmaf(fmaf(fmaf(K.n5, s, K.n4), s, K.n3), s, K.n2), s, K.n1), s, K.n0);
@@ -217,44 +252,99 @@ __device__ __forceinline__ void pair_vjp(const float4 q, const float4 gj, float 
     }
 }
 
-template <int MODE>
+// Per-lane state: K active particles.
+template <int MODE, int K>
 struct WarpState {
-    float xi, yi, zi;
-    float gx, gy, gz;
-    float sx, sy, sz, cx, cy, cz;
-    int npair;
+    float x[K], y[K], z[K];
+    float gx[K], gy[K], gz[K];
+    float sx[K], sy[K], sz[K], cx[K], cy[K], cz[K];
+    int npair[K];
+    int nevals;
     int wr, rd;
 };
 
-template <int MODE>
+// FLAGS bit 0: two partial-sum sets (even / odd ring entries) to halve the
+// dependent FMA chain of the accumulation; summed before the Kahan update.
+template <int MODE, int K, int FLAGS>
 __device__ __forceinline__ void run_batch(const float4* __restrict__ rp, const float4* __restrict__ rg, int cnt,
-                                          WarpState<MODE>& w, const Consts& K) {
-    float px = 0.f, py = 0.f, pz = 0.f;
+                                          WarpState<MODE, K>& w, const Consts& C) {
+    float px[K], py[K], pz[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) px[k] = py[k] = pz[k] = 0.f;
+    if (MODE != kVjp && (FLAGS & 1) && cnt == 32) {
+        constexpr bool CNT = MODE == kForceCount;
+        float qx[K], qy[K], qz[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) qx[k] = qy[k] = qz[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const float4 a0 = rp[j], a1 = rp[j + 1];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                pair_force<CNT>(a0, w.x[k], w.y[k], w.z[k], C, px[k], py[k], pz[k], w.npair[k]);
+                pair_force<CNT>(a1, w.x[k], w.y[k], w.z[k], C, qx[k], qy[k], qz[k], w.npair[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            px[k] += qx[k];
+            py[k] += qy[k];
+            pz[k] += qz[k];
+            kahan_add(w.sx[k], w.cx[k], px[k]);
+            kahan_add(w.sy[k], w.cy[k], py[k]);
+            kahan_add(w.sz[k], w.cz[k], pz[k]);
+        }
+        if (MODE == kForceCount) w.nevals += cnt;
+        return;
+    }
     if (MODE == kVjp) {
         if (cnt == 32) {
 #pragma unroll 8
-            for (int j = 0; j < 32; ++j) pair_vjp(rp[j], rg[j], w.xi, w.yi, w.zi, w.gx, w.gy, w.gz, K, px, py, pz);
+            for (int j = 0; j < 32; ++j) {
+                const float4 q = rp[j], g = rg[j];
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    pair_vjp(q, g, w.x[k], w.y[k], w.z[k], w.gx[k], w.gy[k], w.gz[k], C, px[k], py[k], pz[k]);
+            }
         } else {
-            for (int j = 0; j < cnt; ++j) pair_vjp(rp[j], rg[j], w.xi, w.yi, w.zi, w.gx, w.gy, w.gz, K, px, py, pz);
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = rp[j], g = rg[j];
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    pair_vjp(q, g, w.x[k], w.y[k], w.z[k], w.gx[k], w.gy[k], w.gz[k], C, px[k], py[k], pz[k]);
+            }
         }
     } else {
-        constexpr bool C = MODE == kForceCount;
+        constexpr bool CNT = MODE == kForceCount;
         if (cnt == 32) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) pair_force<C>(rp[j], w.xi, w.yi, w.zi, K, px, py, pz, w.npair);
+            for (int j = 0; j < 32; ++j) {
+                const float4 q = rp[j];
+#pragma unroll
+                for (int k = 0; k < K; ++k) pair_force<CNT>(q, w.x[k], w.y[k], w.z[k], C, px[k], py[k], pz[k], w.npair[k]);
+            }
         } else {
-            for (int j = 0; j < cnt; ++j) pair_force<C>(rp[j], w.xi, w.yi, w.zi, K, px, py, pz, w.npair);
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = rp[j];
+#pragma unroll
+                for (int k = 0; k < K; ++k) pair_force<CNT>(q, w.x[k], w.y[k], w.z[k], C, px[k], py[k], pz[k], w.npair[k]);
+            }
         }
     }
-    kahan_add(w.sx, w.cx, px);
-    kahan_add(w.sy, w.cy, py);
-    kahan_add(w.sz, w.cz, pz);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        kahan_add(w.sx[k], w.cx[k], px[k]);
+        kahan_add(w.sy[k], w.cy[k], py[k]);
+        kahan_add(w.sz[k], w.cz[k], pz[k]);
+    }
+    if (MODE == kForceCount) w.nevals += cnt;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_pairs(const Args a) {
-    __shared__ float4 ring_p[kWarpsPerBlock][kRing];
-    __shared__ float4 ring_g[MODE == kVjp ? kWarpsPerBlock : 1][kRing];
+template <int MODE, int K, int WARPS, int MINB, int FLAGS>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a) {
+    constexpr int C = 32 * K;
+    __shared__ float4 ring_p[WARPS][kRing];
+    __shared__ float4 ring_g[MODE == kVjp ? WARPS : 1][kRing];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -269,107 +359,140 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const Args a) {
         const int I = a.order[it_idx];
         const Item it = load_item(a, I);
         const VolDev& V = a.vols[it.vol];
-        const Consts K = load_consts(V, MODE == kVjp);
-        WarpState<MODE> w;
-        const float4 pi = a.slot_pos[(long long)I * kChunk + lane];
-        w.xi = pi.x; w.yi = pi.y; w.zi = pi.z;
-        w.gx = w.gy = w.gz = 0.f;
-        if (MODE == kVjp) {
-            const float4 gi = a.slot_g[(long long)I * kChunk + lane];
-            w.gx = gi.x; w.gy = gi.y; w.gz = gi.z;
-        }
-        w.sx = w.sy = w.sz = w.cx = w.cy = w.cz = 0.f;
-        w.npair = 0;
-        w.wr = 0; w.rd = 0;
-        for_each_neighbour_chunk(a, it, V, [&](int J, float Sx, float Sy, float Sz, int) {
-            const long long js = (long long)J * kChunk + lane;
-            const float4 pj = a.slot_pos[js];
-            const float xj = pj.x + Sx, yj = pj.y + Sy, zj = pj.z + Sz;
-            const float gx = fmaxf(fmaxf(xj - it.hi[0], it.lo[0] - xj), 0.f);
-            const float gy = fmaxf(fmaxf(yj - it.hi[1], it.lo[1] - yj), 0.f);
-            const float gz = fmaxf(fmaxf(zj - it.hi[2], it.lo[2] - zj), 0.f);
-            const bool keep = gx * gx + gy * gy + gz * gz < K.rcm2;
-            const unsigned m = __ballot_sync(kFull, keep);
-            if (keep) {
-                const int slot = (w.wr + __popc(m & lt)) & (kRing - 1);
-                rp[slot] = make_float4(xj, yj, zj, 0.f);
-                if (MODE == kVjp) rg[slot] = a.slot_g[js];
+        const Consts KC = load_consts(V, MODE == kVjp);
+        WarpState<MODE, K> w;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const long long sl = (long long)I * C + lane + 32 * k;
+            const float4 pi = a.slot_pos[sl];
+            w.x[k] = pi.x; w.y[k] = pi.y; w.z[k] = pi.z;
+            w.gx[k] = w.gy[k] = w.gz[k] = 0.f;
+            if (MODE == kVjp) {
+                const float4 gi = a.slot_g[sl];
+                w.gx[k] = gi.x; w.gy[k] = gi.y; w.gz[k] = gi.z;
             }
-            w.wr += __popc(m);
-            __syncwarp();
-            if (w.wr - w.rd >= 32) {
-                const int base = w.rd & (kRing - 1);
-                run_batch<MODE>(rp + base, rg + base, 32, w, K);
-                w.rd += 32;
+            w.sx[k] = w.sy[k] = w.sz[k] = w.cx[k] = w.cy[k] = w.cz[k] = 0.f;
+            w.npair[k] = 0;
+        }
+        w.nevals = 0;
+        w.wr = 0; w.rd = 0;
+        for_each_neighbour_chunk<K, MODE == kVjp>(a, it, V, [&](int J, float Sx, float Sy, float Sz,
+                                                                const float4* pjs, const float4* gjs) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float4 pj = pjs[k];
+                const float xj = pj.x + Sx, yj = pj.y + Sy, zj = pj.z + Sz;
+                const float gx = fmaxf(fmaxf(xj - it.hi[0], it.lo[0] - xj), 0.f);
+                const float gy = fmaxf(fmaxf(yj - it.hi[1], it.lo[1] - yj), 0.f);
+                const float gz = fmaxf(fmaxf(zj - it.hi[2], it.lo[2] - zj), 0.f);
+                const bool keep = gx * gx + gy * gy + gz * gz < KC.rcm2;
+                const unsigned m = __ballot_sync(kFull, keep);
+                if (keep) {
+                    const int slot = (w.wr + __popc(m & lt)) & (kRing - 1);
+                    rp[slot] = make_float4(xj, yj, zj, 0.f);
+                    if (MODE == kVjp) rg[slot] = gjs[k];
+                }
+                w.wr += __popc(m);
                 __syncwarp();
+                if (w.wr - w.rd >= 32) {
+                    const int base = w.rd & (kRing - 1);
+                    run_batch<MODE, K, FLAGS>(rp + base, rg + base, 32, w, KC);
+                    w.rd += 32;
+                    __syncwarp();
+                }
             }
         });
         if (w.wr > w.rd) {
             const int base = w.rd & (kRing - 1);
-            run_batch<MODE>(rp + base, rg + base, w.wr - w.rd, w, K);
+            run_batch<MODE, K, FLAGS>(rp + base, rg + base, w.wr - w.rd, w, KC);
             __syncwarp();
         }
-        if (lane < it.cnt) {
-            const int orig = a.slot_idx[(long long)I * kChunk + lane];
-            const float ox = (w.sx - w.cx) * K.scale;
-            const float oy = (w.sy - w.cy) * K.scale;
-            const float oz = (w.sz - w.cz) * K.scale;
-            float4* dst = reinterpret_cast<float4*>(a.out) + orig;
-            if (MODE == kVjp && a.accumulate) {
-                const float4 prev = *dst;
-                *dst = make_float4(prev.x + ox, prev.y + oy, prev.z + oz, 0.f);
-            } else {
-                *dst = make_float4(ox, oy, oz, 0.f);
+        int cpairs = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int l = lane + 32 * k;
+            if (l < it.cnt) {
+                const int orig = a.slot_idx[(long long)I * C + l];
+                const float ox = (w.sx[k] - w.cx[k]) * KC.scale;
+                const float oy = (w.sy[k] - w.cy[k]) * KC.scale;
+                const float oz = (w.sz[k] - w.cz[k]) * KC.scale;
+                float4* dst = reinterpret_cast<float4*>(a.out) + orig;
+                if (MODE == kVjp && a.accumulate) {
+                    const float4 prev = *dst;
+                    *dst = make_float4(prev.x + ox, prev.y + oy, prev.z + oz, 0.f);
+                } else {
+                    *dst = make_float4(ox, oy, oz, 0.f);
+                }
+                if (MODE == kForceCount) {
+                    if (a.per_particle) a.per_particle[orig] = w.npair[k] - 1;   // minus the self pair
+                    cpairs += w.npair[k] - 1;
+                }
             }
-            if (MODE == kForceCount && a.per_particle) a.per_particle[orig] = w.npair - 1;
         }
         if (MODE == kForceCount && a.pair_total) {
-            int c = lane < it.cnt ? w.npair - 1 : 0;      // minus the self pair
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-            if (lane == 0) atomicAdd(a.pair_total, (unsigned long long)c);
+            for (int o = 16; o > 0; o >>= 1) cpairs += __shfl_xor_sync(kFull, cpairs, o);
+            if (lane == 0) {
+                atomicAdd(a.pair_total, (unsigned long long)cpairs);
+                atomicAdd(&a.ctr->evals, (unsigned long long)w.nevals * (unsigned long long)it.cnt);
+                atomicAdd(&a.ctr->lane_evals, (unsigned long long)w.nevals * (unsigned long long)C);
+            }
         }
     }
 }
 
-// Cost estimate (pairs the item will evaluate, from chunk-level culling)
-// and the longest-first sort key.  One warp per chunk.
-__global__ void __launch_bounds__(kThreads) k_cost(const Args a, int max_chunks, unsigned* __restrict__ cost,
-                                                   unsigned long long* __restrict__ keys, int* __restrict__ vals) {
-    const int lane = threadIdx.x & 31;
+// Cost estimate of each work item, for the longest-first order: the
+// chunk's particle count times the population of the neighbour cells its
+// box reaches (the same cell culling as the pair kernel).  One thread per
+// chunk; chunks beyond the current count get the lowest priority key.
+__global__ void __launch_bounds__(256) k_cost(const Args a, int max_chunks, unsigned* __restrict__ cost,
+                                              unsigned long long* __restrict__ keys, int* __restrict__ vals) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= max_chunks) return;
     const int n_chunks = a.ccs[a.total_cells];
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int I = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); I < max_chunks; I += warps) {
-        if (I >= n_chunks) {
-            if (lane == 0) { keys[I] = 255ull; vals[I] = I; }
-            continue;
-        }
-        const Item it = load_item(a, I);
-        const VolDev& V = a.vols[it.vol];
-        unsigned long long sum = 0;
-        for_each_neighbour_chunk(a, it, V, [&](int, float, float, float, int cj) { sum += (unsigned)cj; });
-        if (lane == 0) {
-            unsigned long long c = sum * (unsigned long long)it.cnt;
-            if (c > 0xffffffffull) c = 0xffffffffull;
-            cost[I] = (unsigned)c;
-            atomicAdd(&a.ctr->cost_total, c);
-            // quarter-octave bucket of the cost, largest first
-            const unsigned long long x = c + 1;
-            const int msb = 63 - __clzll((long long)x);
-            const int frac = msb >= 2 ? (int)((x >> (msb - 2)) & 3) : (int)((x << (2 - msb)) & 3);
-            int bucket = msb * 4 + frac;
-            if (bucket > 254) bucket = 254;
-            keys[I] = (unsigned long long)(254 - bucket);
-            vals[I] = I;
+    if (I >= n_chunks) {
+        keys[I] = 255ull;
+        vals[I] = I;
+        return;
+    }
+    const Item it = load_item(a, I);
+    const VolDev& V = a.vols[it.vol];
+    int c[3], olo[3], ohi[3];
+    cell_range(it, V, c, olo, ohi);
+    unsigned long long sum = 0;
+    for (int oz = olo[2]; oz <= ohi[2]; ++oz) {
+        int nz = c[2] + oz;
+        nz += nz < 0 ? V.n_c : (nz >= V.n_c ? -V.n_c : 0);
+        for (int oy = olo[1]; oy <= ohi[1]; ++oy) {
+            int ny = c[1] + oy;
+            ny += ny < 0 ? V.n_c : (ny >= V.n_c ? -V.n_c : 0);
+            for (int ox = olo[0]; ox <= ohi[0]; ++ox) {
+                int nx = c[0] + ox;
+                nx += nx < 0 ? V.n_c : (nx >= V.n_c ? -V.n_c : 0);
+                const int cell = V.cell_base + (nz * V.n_c + ny) * V.n_c + nx;
+                sum += (unsigned)(a.cell_start[cell + 1] - a.cell_start[cell]);
+            }
         }
     }
+    unsigned long long cst = sum * (unsigned long long)it.cnt;
+    if (cst > 0xffffffffull) cst = 0xffffffffull;
+    cost[I] = (unsigned)cst;
+    atomicAdd(&a.ctr->cost_total, cst);
+    // quarter-octave bucket of the cost, largest first
+    const unsigned long long x = cst + 1;
+    const int msb = 63 - __clzll((long long)x);
+    const int frac = msb >= 2 ? (int)((x >> (msb - 2)) & 3) : (int)((x << (2 - msb)) & 3);
+    int bucket = msb * 4 + frac;
+    if (bucket > 254) bucket = 254;
+    keys[I] = (unsigned long long)(254 - bucket);
+    vals[I] = I;
 }
 
 __global__ void __launch_bounds__(256) k_gather_g(const float* __restrict__ g, const int* __restrict__ slot_idx,
-                                                  const int* __restrict__ ccs, int total_cells, float scale,
-                                                  float4* __restrict__ slot_g) {
+                                                  const int* __restrict__ ccs, int total_cells, int chunk,
+                                                  float scale, float4* __restrict__ slot_g) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n_slots = (long long)ccs[total_cells] * kChunk;
+    const long long n_slots = (long long)ccs[total_cells] * chunk;
     if (s >= n_slots) return;
     const int idx = slot_idx[s];
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -383,6 +506,7 @@ __global__ void __launch_bounds__(256) k_gather_g(const float* __restrict__ g, c
 Args make_args(sr_plan* p) {
     Args a{};
     a.ccs = p->ccs;
+    a.cell_start = p->cell_start;
     a.total_cells = (int)p->total_cells;
     a.meta = p->chunk_meta;
     a.clo = p->chunk_lo;
@@ -396,25 +520,57 @@ Args make_args(sr_plan* p) {
     return a;
 }
 
-template <int MODE>
-int occupancy_blocks(sr_plan* p) {
+template <int MODE, int K, int WARPS, int MINB, int FLAGS>
+int occ(sr_plan* p) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<MODE>, kThreads, 0);
-    if (e != cudaSuccess) return -(int)e;
-    if (per_sm < 1) per_sm = 1;
-    return per_sm * p->sm_count;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<MODE, K, WARPS, MINB, FLAGS>,
+                                                                  WARPS * 32, 0);
+    if (e != cudaSuccess) return -1;
+    return (per_sm < 1 ? 1 : per_sm) * p->sm_count;
+}
+
+// Force-kernel variants: (warps per block, min blocks per SM, flags).
+//   0: 8 x 1   1: 8 x 2   2: 8 x 3   3: 8 x 4
+//   4: 4 x 6 + split sums   5: 4 x 7 + split sums   6: 8 x 3 + split sums   7: 8 x 2 + split sums
+#define SR_FORCE_VARIANTS(X) \
+    X(0, 8, 1, 0) X(1, 8, 2, 0) X(2, 8, 3, 0) X(3, 8, 4, 0) \
+    X(4, 4, 6, 1) X(5, 4, 7, 1) X(6, 8, 3, 1) X(7, 8, 2, 1)
+
+template <int K>
+int occupancy_k(sr_plan* p) {
+    int v[kVariants];
+#define SR_OCC(I, W, B, F) v[I] = occ<kForce, K, W, B, F>(p);
+    SR_FORCE_VARIANTS(SR_OCC)
+#undef SR_OCC
+    const int c = occ<kForceCount, K, 8, 1, 0>(p), g = occ<kVjp, K, 8, 1, 0>(p);
+    for (int i = 0; i < kVariants; ++i)
+        if (v[i] < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
+    if (c < 0 || g < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
+    for (int i = 0; i < kVariants; ++i) p->force_blocks_v[i] = v[i];
+    p->count_blocks = c;
+    p->vjp_blocks = g;
+    return SR_OK;
+}
+
+template <int K>
+void launch_force_k(sr_plan* p, const Args& a, cudaStream_t st) {
+    const int blocks = p->force_blocks_v[p->variant];
+    switch (p->variant) {
+#define SR_LAUNCH(I, W, B, F) \
+    case I: k_pairs<kForce, K, W, B, F><<<blocks, W * 32, 0, st>>>(a); break;
+        SR_FORCE_VARIANTS(SR_LAUNCH)
+#undef SR_LAUNCH
+        default: break;
+    }
 }
 
 }  // namespace
 
+// Pair-kernel variants selectable per plan (the autotuner times them).
 int force_occupancy(sr_plan* p) {
-    int b0 = occupancy_blocks<kForce>(p);
-    int b1 = occupancy_blocks<kForceCount>(p);
-    int b2 = occupancy_blocks<kVjp>(p);
-    if (b0 < 0 || b1 < 0 || b2 < 0) return set_error(SR_ERR_CUDA, "cudaOccupancyMaxActiveBlocksPerMultiprocessor failed");
-    p->force_blocks = b0;
-    p->count_blocks = b1;
-    p->vjp_blocks = b2;
+    const int rc = p->chunk_k == 2 ? occupancy_k<2>(p) : occupancy_k<1>(p);
+    if (rc) return rc;
+    p->force_blocks = p->force_blocks_v[p->variant];
     p->warps_per_block = kWarpsPerBlock;
     return SR_OK;
 }
@@ -423,10 +579,7 @@ int launch_cost_and_order(sr_plan* p, cudaStream_t st) {
     Args a = make_args(p);
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->cost_total, 0, sizeof(unsigned long long), st));
     const long long mc = p->max_chunks;
-    long long want = (mc + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    long long cap = (long long)p->sm_count * 8;
-    const int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    k_cost<<<blocks, kThreads, 0, st>>>(a, (int)mc, p->cost, p->lpt_keys[0], p->lpt_vals[0]);
+    k_cost<<<(int)((mc + 255) / 256), 256, 0, st>>>(a, (int)mc, p->cost, p->lpt_keys[0], p->lpt_vals[0]);
     SR_LAUNCH_CHECK("k_cost");
     int which = 0;
     int rc = radix_sort_pairs(p->lpt_keys, p->lpt_vals, (int)mc, 8, p->rs_chunks, st, &which);
@@ -442,25 +595,30 @@ int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_par
     a.pair_total = pairs;
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->queue, 0, sizeof(long long), st));
     if (pairs || per_particle) {
-        k_pairs<kForceCount><<<p->count_blocks, kThreads, 0, st>>>(a);
+        SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->evals, 0, 2 * sizeof(unsigned long long), st));
+        if (p->chunk_k == 2) k_pairs<kForceCount, 2, 8, 1, 0><<<p->count_blocks, kThreads, 0, st>>>(a);
+        else k_pairs<kForceCount, 1, 8, 1, 0><<<p->count_blocks, kThreads, 0, st>>>(a);
         SR_LAUNCH_CHECK("k_pairs<count>");
-    } else {
-        k_pairs<kForce><<<p->force_blocks, kThreads, 0, st>>>(a);
-        SR_LAUNCH_CHECK("k_pairs<force>");
+        return SR_OK;
     }
+    if (p->chunk_k == 2) launch_force_k<2>(p, a, st);
+    else launch_force_k<1>(p, a, st);
+    SR_LAUNCH_CHECK("k_pairs<force>");
     return SR_OK;
 }
 
 int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int accumulate, cudaStream_t st) {
-    const long long n_slots = p->max_chunks * kChunk;
+    const int C = 32 * p->chunk_k;
+    const long long n_slots = p->max_chunks * C;
     k_gather_g<<<(int)((n_slots + 255) / 256), 256, 0, st>>>(g_acc, p->slot_idx, p->ccs, (int)p->total_cells,
-                                                             g_scale, p->slot_g);
+                                                             C, g_scale, p->slot_g);
     SR_LAUNCH_CHECK("k_gather_g");
     Args a = make_args(p);
     a.out = g_pos;
     a.accumulate = accumulate;
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->queue, 0, sizeof(long long), st));
-    k_pairs<kVjp><<<p->vjp_blocks, kThreads, 0, st>>>(a);
+    if (p->chunk_k == 2) k_pairs<kVjp, 2, 8, 1, 0><<<p->vjp_blocks, kThreads, 0, st>>>(a);
+    else k_pairs<kVjp, 1, 8, 1, 0><<<p->vjp_blocks, kThreads, 0, st>>>(a);
     SR_LAUNCH_CHECK("k_pairs<vjp>");
     return SR_OK;
 }

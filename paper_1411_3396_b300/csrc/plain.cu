@@ -15,12 +15,12 @@ __global__ void __launch_bounds__(128) k_plain(const int* __restrict__ ccs, cons
                                                const float4* __restrict__ clo,
                                                const float4* __restrict__ slot_pos,
                                                const int* __restrict__ slot_idx,
-                                               const VolDev* __restrict__ vols, long long slot_begin,
+                                               const VolDev* __restrict__ vols, int chunk, long long slot_begin,
                                                long long slot_end, float4* __restrict__ acc) {
     const long long s = slot_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= slot_end) return;
-    const int I = (int)(s / kChunk);
-    const int lane = (int)(s % kChunk);
+    const int I = (int)(s / chunk);
+    const int lane = (int)(s % chunk);
     const int4 mi = meta[I];
     const int cnt = __float_as_int(clo[I].w);
     if (lane >= cnt) return;
@@ -49,14 +49,15 @@ __global__ void __launch_bounds__(128) k_plain(const int* __restrict__ ccs, cons
                     const float Sz = (float)(mj.z + wz * V.M - mi.z);
                     float px = 0.f, py = 0.f, pz = 0.f;
                     for (int l = 0; l < cj; ++l) {
-                        const float4 pj = slot_pos[(long long)J * kChunk + l];
+                        const float4 pj = slot_pos[(long long)J * chunk + l];
                         const float dx = (pj.x + Sx) - pi.x;
                         const float dy = (pj.y + Sy) - pi.y;
                         const float dz = (pj.z + Sz) - pi.z;
                         float q = fmaf(dx, dx, eps2);
                         q = fmaf(dy, dy, q);
                         q = fmaf(dz, dz, q);
-                        const float r = rsqrtf(q);
+                        float r;
+                        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
                         const float r2 = r * r;
                         const float nq = fmaf(fmaf(fmaf(fmaf(fmaf(n5, q, n4), q, n3), q, n2), q, n1), q, n0);
                         const float f = fmaf(r2, r, nq);
@@ -84,15 +85,16 @@ int launch_force_plain(sr_plan* p, float* acc, cudaStream_t st) {
     std::vector<int> ccs(tc + 1);
     SR_CUDA_CHECK(cudaMemcpyAsync(ccs.data(), p->ccs, sizeof(int) * (tc + 1), cudaMemcpyDeviceToHost, st));
     SR_CUDA_CHECK(cudaStreamSynchronize(st));
+    const int C = 32 * p->chunk_k;
     for (const VolDev& V : p->vols_h) {
         const long long slab = (long long)V.n_c * V.n_c;
         for (int cz = 0; cz < V.n_c; ++cz) {
             const long long c0 = V.cell_base + cz * slab, c1 = c0 + slab;
-            const long long s0 = (long long)ccs[c0] * kChunk, s1 = (long long)ccs[c1] * kChunk;
+            const long long s0 = (long long)ccs[c0] * C, s1 = (long long)ccs[c1] * C;
             if (s1 <= s0) continue;
             const int blocks = (int)((s1 - s0 + 127) / 128);
             k_plain<<<blocks, 128, 0, st>>>(p->ccs, p->chunk_meta, p->chunk_lo, p->slot_pos, p->slot_idx,
-                                            p->vols, s0, s1, reinterpret_cast<float4*>(acc));
+                                            p->vols, C, s0, s1, reinterpret_cast<float4*>(acc));
             SR_LAUNCH_CHECK("k_plain");
         }
     }

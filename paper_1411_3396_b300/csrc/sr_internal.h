@@ -11,19 +11,23 @@
 
 namespace sr {
 
-constexpr int kChunk = 32;          // particles per chunk = lanes per warp
+constexpr int kMaxChunkK = 2;       // chunks hold 32 K particles, K = 1 or 2 (K per lane)
 constexpr float kPad = 1.0e30f;     // coordinate of an empty slot: never within r_c
 constexpr int kScanItems = 8;       // items per thread in scans / radix passes
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBuckets = 1 << kRadixBits;
+constexpr int kVariants = 8;        // force-kernel variants (launch shape / accumulation)
 
 // Per-volume constants, device resident, read once per work item.
 // Lengths inside kernels are in units of the fine grid h = L / (n_c 2^b).
 struct VolDev {
     double box;          // L
     double h;            // fine cell side, L / M
+    double inv_h;        // 1/h, used instead of a division when h is a power of two
+    int h_pow2;          // 1 if h is an exact power of two (then x * inv_h == x / h)
+    int pad1;
     long long part_start;  // first caller row of the volume
     long long part_end;
     int n_c;             // cells per axis
@@ -46,7 +50,9 @@ struct Counters {
     long long queue;          // next work item of the persistent kernels
     long long err;            // bit 0: bad position seen by sr_bin
     unsigned long long cost_total;
-    long long reserved[5];
+    unsigned long long evals;         // counting variant: candidate (i, j) evaluations, valid i only
+    unsigned long long lane_evals;    // counting variant: candidate evaluations x 32 lanes
+    long long reserved[3];
 };
 
 struct ScanScratch {
@@ -70,6 +76,7 @@ struct sr_plan {
     long long n_binned = 0;
     bool binned = false;
     int sub_bits = 6;
+    int chunk_k = 2;                       // particles per lane; chunk size = 32 * chunk_k
     int key_bits = 0;
     long long total_cells = 0;
     long long max_chunks = 0;
@@ -88,6 +95,7 @@ struct sr_plan {
     int* cell_start = nullptr;             // total_cells + 1
     int* cell_nch = nullptr;               // total_cells + 1
     int* ccs = nullptr;                    // cell -> first chunk, total_cells + 1
+    int* chunk_cell = nullptr;             // chunk -> cell
     int4* chunk_meta = nullptr;            // anchor qx, qy, qz, volume
     float4* chunk_lo = nullptr;            // bbox min, w = count (int bits)
     float4* chunk_hi = nullptr;
@@ -110,10 +118,12 @@ struct sr_plan {
     float* h_acc_dev = nullptr;
 
     int sm_count = 0;
+    int variant = 0;                       // pair-kernel variant (launch bounds), see force.cu
     int force_blocks = 0;
+    int force_blocks_v[sr::kVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
     int vjp_blocks = 0;
     int count_blocks = 0;
-    int warps_per_block = 8;
+    int warps_per_block = 8;               // of the selected force variant
 };
 
 namespace sr {

@@ -31,21 +31,21 @@ def assert_force_close(a_gpu, a_ref, what=""):
     return med, mx
 
 
-def make_plan(vols, params, sub_bits=0, n_cells=None):
+def make_plan(vols, params, sub_bits=0, n_cells=None, chunk_size=0):
     """Plan for a list of (positions, box) volumes with physics params."""
     from paper_1411_3396_b300 import Plan
     if len(vols) == 1:
         pos, box = vols[0]
         return Plan(box, params["rc"], params["eps"], params["sigma"], len(pos),
-                    n_cells=(n_cells or [0])[0], sub_bits=sub_bits)
+                    n_cells=(n_cells or [0])[0], sub_bits=sub_bits, chunk_size=chunk_size)
     return Plan.batch([b for _, b in vols], [len(p) for p, _ in vols], params["rc"], params["eps"],
-                      params["sigma"], n_cells=n_cells, sub_bits=sub_bits)
+                      params["sigma"], n_cells=n_cells, sub_bits=sub_bits, chunk_size=chunk_size)
 
 
 def oracle_binning(plan, vols):
     info = plan.info()
     cells = [plan.volume(v)["n_cells"] for v in range(len(vols))]
-    return obin.bin_particles(vols, cells, info["sub_bits"])
+    return obin.bin_particles(vols, cells, info["sub_bits"], info["chunk_size"])
 
 
 def oracle_force(vols, params):

@@ -40,19 +40,22 @@ def _compare(plan, vols):
     np.testing.assert_array_equal(lo[:, 3].view(np.int32), B["chunk_count"])
 
 
+@pytest.mark.parametrize("chunk", [32, 64])
 @pytest.mark.parametrize("name", ["uniform4k", "zeldovich128", "clustered256", "batch64"])
-def test_bin_bit_exact_small(name):
+def test_bin_bit_exact_small(name, chunk):
     cfg = wc.small_variant(name)
     w = wc.make_workload(cfg)
-    plan = _run_bin(w["volumes"], w["params"])
+    plan = _run_bin(w["volumes"], w["params"], chunk_size=chunk)
+    assert plan.info()["chunk_size"] == chunk
     _compare(plan, w["volumes"])
 
 
-@pytest.mark.parametrize("sub_bits,n_cells", [(1, 0), (4, 3), (8, 5)])
-def test_bin_geometry_variants(sub_bits, n_cells):
+@pytest.mark.parametrize("sub_bits,n_cells,chunk", [(1, 0, 32), (4, 3, 64), (8, 5, 32), (6, 4, 64)])
+def test_bin_geometry_variants(sub_bits, n_cells, chunk):
     pos = gen.uniform_box(3000, 17.0, 21)            # h not a power of two
     vols = [(pos, 17.0)]
-    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), sub_bits=sub_bits, n_cells=[n_cells])
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), sub_bits=sub_bits, n_cells=[n_cells],
+                    chunk_size=chunk)
     _compare(plan, vols)
 
 
@@ -93,6 +96,8 @@ def test_bin_capacity_errors():
         Plan(16.0, 3.0, 0.0, 0.8, 100)               # eps must be > 0
     with pytest.raises(SrError):
         Plan(16.0, 3.0, 0.1, 0.8, 100, n_cells=6)    # cell side 2.67 < r_c
+    with pytest.raises(SrError):
+        Plan(16.0, 3.0, 0.1, 0.8, 100, chunk_size=48)
 
 
 def test_bin_partial_fill_and_rebin():

@@ -31,16 +31,25 @@ def _gpu(vols, params, count=True, **kw):
     return plan, to_np(acc), None, None
 
 
-@pytest.fixture(scope="module", params=SMALL)
+_WORK = {}
+
+
+def _work(name):
+    if name not in _WORK:
+        _WORK[name] = wc.make_workload(wc.small_variant(name))
+    return _WORK[name]
+
+
+@pytest.fixture(scope="module", params=[(n, c) for n in SMALL for c in (32, 64)],
+                ids=lambda p: f"{p[0]}-c{p[1]}")
 def small_case(request):
-    cfg = wc.small_variant(request.param)
-    w = wc.make_workload(cfg)
-    return request.param, w
+    name, chunk = request.param
+    return name, _work(name), chunk
 
 
 def test_force_matches_oracle(small_case):
-    name, w = small_case
-    plan, acc, pairs, pp = _gpu(w["volumes"], w["params"])
+    name, w, chunk = small_case
+    plan, acc, pairs, pp = _gpu(w["volumes"], w["params"], chunk_size=chunk)
     a_ref, _ = oracle_force(w["volumes"], w["params"])
     assert_force_close(acc, a_ref, name)
     assert np.all(acc[:, 3] == 0)
@@ -48,8 +57,8 @@ def test_force_matches_oracle(small_case):
 
 def test_force_matches_oracle_on_dequantised_positions(small_case):
     # the kernel arithmetic alone (same binary32 inputs as the GPU)
-    name, w = small_case
-    plan, acc, _, _ = _gpu(w["volumes"], w["params"], count=False)
+    name, w, chunk = small_case
+    plan, acc, _, _ = _gpu(w["volumes"], w["params"], count=False, chunk_size=chunk)
     B = oracle_binning(plan, w["volumes"])
     xr = obin.dequantized_positions(B, w["volumes"])
     vols_r, k = [], 0
@@ -62,25 +71,39 @@ def test_force_matches_oracle_on_dequantised_positions(small_case):
 
 
 def test_pair_counts_bit_exact(small_case):
-    name, w = small_case
-    plan, acc, pairs, pp = _gpu(w["volumes"], w["params"])
+    name, w, chunk = small_case
+    plan, acc, pairs, pp = _gpu(w["volumes"], w["params"], chunk_size=chunk)
     B = oracle_binning(plan, w["volumes"])
     ref = oforce.pair_counts_fp32(B, w["volumes"], w["params"]["rc"], w["params"]["eps"])
     np.testing.assert_array_equal(pp, ref)
     assert pairs == int(ref.sum())
 
 
-def test_counting_variant_gives_same_forces(small_case):
-    name, w = small_case
-    _, acc1, _, _ = _gpu(w["volumes"], w["params"], count=False)
-    _, acc2, _, _ = _gpu(w["volumes"], w["params"], count=True)
-    assert acc1.tobytes() == acc2.tobytes()
+def test_all_kernel_variants_give_identical_forces(small_case):
+    # variants 0-3 share the summation order of the counting kernel; 4-7
+    # add even and odd neighbours separately (identical among themselves)
+    name, w, chunk = small_case
+    plan, acc_c, _, _ = _gpu(w["volumes"], w["params"], count=True, chunk_size=chunk)
+    ref = acc_c.tobytes()
+    for v in range(4):
+        plan.set_variant(v)
+        acc = to_np(plan.force())
+        assert acc.tobytes() == ref, f"variant {v}"
+    split = None
+    for v in range(4, 8):
+        plan.set_variant(v)
+        acc = to_np(plan.force())
+        if split is None:
+            split = acc
+            a_ref, _ = oracle_force(w["volumes"], w["params"])
+            assert_force_close(acc, a_ref, f"{name} variant {v}")
+        assert acc.tobytes() == split.tobytes(), f"variant {v}"
 
 
 def test_plain_kernel_matches_oracle(small_case):
-    name, w = small_case
+    name, w, chunk = small_case
     pos = np.concatenate([p for p, _ in w["volumes"]])
-    plan = make_plan(w["volumes"], w["params"])
+    plan = make_plan(w["volumes"], w["params"], chunk_size=chunk)
     plan.bin(torch.from_numpy(pos).cuda())
     acc = to_np(plan.force_plain())
     a_ref, _ = oracle_force(w["volumes"], w["params"])
@@ -88,7 +111,7 @@ def test_plain_kernel_matches_oracle(small_case):
 
 
 def test_force_is_deterministic():
-    w = wc.make_workload(wc.small_variant("clustered256"))
+    w = _work("clustered256")
     pos = torch.from_numpy(np.concatenate([p for p, _ in w["volumes"]])).cuda()
     plan = make_plan(w["volumes"], w["params"])
     outs = []
@@ -133,7 +156,7 @@ def test_single_particle_and_far_pair():
 
 
 def test_newton_third_law_on_gpu():
-    w = wc.make_workload(wc.small_variant("clustered256"))
+    w = _work("clustered256")
     plan, acc, _, _ = _gpu(w["volumes"], w["params"], count=False)
     vel = torch.zeros((acc.shape[0], 4), dtype=torch.float32, device="cuda")
     inv = to_np(plan.invariants(vel, torch.from_numpy(acc).cuda()))
