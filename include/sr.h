@@ -218,7 +218,8 @@ int sr_kick(int64_t n, const float* acc, float* vel, float dt, void* stream);
 
 /*
  * sr_drift -- x <- fold(x + v dt) in binary64 for the plan's volumes
- * (x + double(v) * dt, then x<0: x+L, x>=L: x-L).  pos: device binary64
+ * (t = double(v) * dt and x + t, each rounded once (no fused multiply-add),
+ * then x<0: x+L, x>=L: x-L).  pos: device binary64
  * rows (x, y, z), updated in place; vel: device float4 rows; n as for
  * sr_bin.  Errors: SR_ERR_ARG, SR_ERR_CAPACITY.
  */
@@ -280,6 +281,22 @@ int sr_plan_set_variant(sr_plan* plan, int variant);
  * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG, SR_ERR_CUDA.
  */
 int sr_autotune(sr_plan* plan, float* acc, int reps, float* ms_out, void* stream);
+
+/*
+ * sr_graph_capture -- record one whole step (sr_bin of pos, sr_force into
+ * acc, sr_kick of vel by dt, for n particles) on stream into a CUDA graph
+ * owned by the plan, replacing any earlier one.  Nothing runs during the
+ * capture.  pos, vel, acc: device buffers that every replay reads and
+ * writes in place (refill their contents, keep the pointers).  stream must
+ * not be the legacy default stream (NULL), which cannot be captured.
+ * Errors: SR_ERR_ARG (null pointers or stream), SR_ERR_CAPACITY, SR_ERR_CUDA.
+ */
+int sr_graph_capture(sr_plan* plan, const double* pos, float* vel, float* acc, float dt, int64_t n,
+                     void* stream);
+
+/* sr_graph_launch -- replay the captured step on stream (one graph launch).
+ * Errors: SR_ERR_STATE if nothing was captured, SR_ERR_CUDA. */
+int sr_graph_launch(sr_plan* plan, void* stream);
 
 /* sr_last_error -- message of the last failure on this thread ("" if none). */
 const char* sr_last_error(void);

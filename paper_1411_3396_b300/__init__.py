@@ -6,5 +6,6 @@ VJP -- runs in the CUDA kernels of ``libsr_b300.so`` (sources in ``csrc/``,
 C ABI in ``include/sr.h``).  This package only marshals tensors.
 """
 from .api import Plan, fit_poly, kick, launch_count  # noqa: F401
+from .autograd import trajectory  # noqa: F401
 from ._lib import SrError  # noqa: F401
 from .build import LIB, build  # noqa: F401

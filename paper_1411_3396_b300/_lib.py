@@ -54,6 +54,8 @@ SIGNATURES = {
     "sr_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
     "sr_plan_set_variant": (c_int, [c_void_p, c_int]),
     "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
+    "sr_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
+    "sr_graph_launch": (c_int, [c_void_p, c_void_p]),
     "sr_last_error": (c_char_p, []),
     "sr_launch_count": (c_int64, []),
 }

@@ -185,6 +185,19 @@ class Plan:
         check(load().sr_autotune(self._h, _ptr(acc), int(reps), ms, _stream()))
         return list(ms)
 
+    def graph_capture(self, pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, dt: float):
+        """Capture bin + force + kick on the current (non-default) stream into
+        a plan-owned CUDA graph; replay with graph_launch()."""
+        _need(pos, torch.float64, 3, "pos")
+        _need(vel, torch.float32, 4, "vel", pos.shape[0])
+        _need(acc, torch.float32, 4, "acc", pos.shape[0])
+        check(load().sr_graph_capture(self._h, _ptr(pos), _ptr(vel), _ptr(acc), float(dt), pos.shape[0],
+                                      _stream()))
+        self.n = pos.shape[0]
+
+    def graph_launch(self):
+        check(load().sr_graph_launch(self._h, _stream()))
+
     def status(self):
         check(load().sr_plan_status(self._h, _stream()))
 

@@ -29,6 +29,7 @@ int dalloc(T** p, size_t count) {
 
 void free_plan(sr_plan* p) {
     if (!p) return;
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     cudaFree(p->vols);
     cudaFree(p->vol_part_start);
     cudaFree(p->vol_cell_base);
@@ -477,6 +478,43 @@ int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
     p->variant = best_v;
     p->force_blocks = p->force_blocks_v[best_v];
     return rc;
+}
+
+int sr_graph_capture(sr_plan* p, const double* pos, float* vel, float* acc, float dt, int64_t n, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!pos || !vel || !acc) return set_error(SR_ERR_ARG, "null buffer");
+    if (!stream) return set_error(SR_ERR_ARG, "the legacy default stream cannot be captured");
+    if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    if (p->n_vol > 1 && n != p->capacity)
+        return set_error(SR_ERR_CAPACITY, "a batch plan bins exactly the sum of its volume counts");
+    cudaStream_t st = as_stream(stream);
+    SR_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_bin(p, pos, n, st);
+    if (!rc) rc = launch_force(p, acc, nullptr, nullptr, st);
+    if (!rc) rc = launch_kick(n, acc, vel, dt, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = ex;
+    p->n_binned = n;
+    p->binned = true;
+    return SR_OK;
+}
+
+int sr_graph_launch(sr_plan* p, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->graph_exec) return set_error(SR_ERR_STATE, "no captured graph");
+    SR_CUDA_CHECK(cudaGraphLaunch(p->graph_exec, as_stream(stream)));
+    return SR_OK;
 }
 
 const char* sr_last_error(void) { return g_last_error.c_str(); }

@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(256) k_drift(long long n, double* __restrict__
         const double vv[3] = {(double)v.x, (double)v.y, (double)v.z};
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            double x = pos[3 * i + ax] + vv[ax] * dt;
+            // x + v dt as two correctly rounded operations (no fused multiply-add)
+            double x = __dadd_rn(pos[3 * i + ax], __dmul_rn(vv[ax], dt));
             if (x < 0.0) x = x + box;
             if (x >= box) x = x - box;
             pos[3 * i + ax] = x;

@@ -112,6 +112,9 @@ struct sr_plan {
     sr::RadixScratch rs_chunks;
     sr::ScanScratch scan_cells;
 
+    // captured whole-step graph (sr_graph_capture)
+    cudaGraphExec_t graph_exec = nullptr;
+
     // staging for sr_step_host
     double* h_pos_dev = nullptr;
     float* h_vel_dev = nullptr;
