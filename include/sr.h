@@ -76,7 +76,7 @@ typedef struct sr_params {
     int    fit_mode;  /* SR_FIT_CONSTRAINED or SR_FIT_UNCONSTRAINED                    */
     int    n_cells;   /* cells per axis; 0 = automatic (side close to 4, >= r_c)        */
     int    sub_bits;  /* Morton bits per axis inside a cell (1..8); 0 = automatic (6)  */
-    int    chunk_size;/* particles per chunk: 32 or 64; 0 = automatic (64)             */
+    int    chunk_size;/* particles per chunk: 32 or 64; 0 = automatic (32)             */
 } sr_params;
 
 /* Read-only description of a plan (sizes of the exportable arrays). */
@@ -264,11 +264,12 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  * (same arithmetic and summation order, different launch shape):
  *   0..3: 256-thread blocks, at least 1, 2, 3, 4 resident per SM
  *         (register budgets 255, 128, 85, 64 per thread);
- *   4, 5: 128-thread blocks, at least 6, 7 per SM, split partial sums;
- *   6, 7: 256-thread blocks, at least 3, 2 per SM, split partial sums.
- * Split partial sums add even and odd neighbours of a 32-neighbour batch
- * separately before the compensated update, so results differ from
- * variants 0..3 in the last bits.  Errors: SR_ERR_ARG.
+ *   4..6: 128-thread blocks, at least 6, 7, 8 resident per SM
+ *         (register budgets 85, 73, 64);
+ *   7:    as 2, with split partial sums.
+ * Variants 0..6 are bit-identical.  Split partial sums add even and odd
+ * neighbours of a 32-neighbour batch separately before the compensated
+ * update, so variant 7 differs in the last bits.  Errors: SR_ERR_ARG.
  */
 int sr_plan_set_variant(sr_plan* plan, int variant);
 

@@ -12,7 +12,7 @@ namespace sr {
 namespace {
 thread_local std::string g_last_error;
 
-int variant_warps(int v) { return (v == 4 || v == 5) ? 4 : 8; }
+int variant_warps(int v) { return (v >= 4 && v <= 6) ? 4 : 8; }
 std::atomic<long long> g_launches{0};
 
 constexpr double kSideMargin = 1.0 + 1.0 / (1 << 20);   // cell side must exceed r_c by this factor
@@ -150,7 +150,7 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
     p->n_vol = n_vol;
     p->capacity = cap;
     p->sub_bits = params[0].sub_bits ? params[0].sub_bits : 6;
-    p->chunk_k = params[0].chunk_size == 32 ? 1 : 2;
+    p->chunk_k = params[0].chunk_size == 64 ? 2 : 1;
     const long long C = 32 * p->chunk_k;
     if ((rc = fit_poly(params[0].r_c, params[0].sigma, params[0].eps, params[0].fit_mode, p->coef))) {
         delete p;

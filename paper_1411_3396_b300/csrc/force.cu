@@ -340,8 +340,10 @@ __device__ __forceinline__ void run_batch(const float4* __restrict__ rp, const f
     if (MODE == kForceCount) w.nevals += cnt;
 }
 
-template <int MODE, int K, int WARPS, int MINB, int FLAGS>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a) {
+// SINGLE: one-volume plans read the volume constants from the kernel
+// parameter (constant bank, no registers); batches read them per item.
+template <int MODE, int K, int WARPS, int MINB, int FLAGS, bool SINGLE>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const VolDev v0) {
     constexpr int C = 32 * K;
     __shared__ float4 ring_p[WARPS][kRing];
     __shared__ float4 ring_g[MODE == kVjp ? WARPS : 1][kRing];
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a) {
         if (it_idx >= n_items) break;
         const int I = a.order[it_idx];
         const Item it = load_item(a, I);
-        const VolDev& V = a.vols[it.vol];
+        const VolDev& V = SINGLE ? v0 : a.vols[it.vol];
         const Consts KC = load_consts(V, MODE == kVjp);
         WarpState<MODE, K> w;
 #pragma unroll
@@ -520,29 +522,32 @@ Args make_args(sr_plan* p) {
     return a;
 }
 
-template <int MODE, int K, int WARPS, int MINB, int FLAGS>
+template <int MODE, int K, int WARPS, int MINB, int FLAGS, bool SINGLE>
 int occ(sr_plan* p) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<MODE, K, WARPS, MINB, FLAGS>,
-                                                                  WARPS * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_pairs<MODE, K, WARPS, MINB, FLAGS, SINGLE>, WARPS * 32, 0);
     if (e != cudaSuccess) return -1;
     return (per_sm < 1 ? 1 : per_sm) * p->sm_count;
 }
 
-// Force-kernel variants: (warps per block, min blocks per SM, flags).
-//   0: 8 x 1   1: 8 x 2   2: 8 x 3   3: 8 x 4
-//   4: 4 x 6 + split sums   5: 4 x 7 + split sums   6: 8 x 3 + split sums   7: 8 x 2 + split sums
+// Force-kernel variants (warps per block, min blocks per SM, flags):
+//   0: 8 x 1   1: 8 x 2   2: 8 x 3   3: 8 x 4   (register budgets 255, 128, 85, 64)
+//   4: 4 x 6   5: 4 x 7   6: 4 x 8              (85, 73, 64)
+//   7: 8 x 3 with split partial sums (even / odd neighbours)
 #define SR_FORCE_VARIANTS(X) \
     X(0, 8, 1, 0) X(1, 8, 2, 0) X(2, 8, 3, 0) X(3, 8, 4, 0) \
-    X(4, 4, 6, 1) X(5, 4, 7, 1) X(6, 8, 3, 1) X(7, 8, 2, 1)
+    X(4, 4, 6, 0) X(5, 4, 7, 0) X(6, 4, 8, 0) X(7, 8, 3, 1)
 
-template <int K>
+int variant_warps_of(int v) { return (v >= 4 && v <= 6) ? 4 : 8; }
+
+template <int K, bool SINGLE>
 int occupancy_k(sr_plan* p) {
     int v[kVariants];
-#define SR_OCC(I, W, B, F) v[I] = occ<kForce, K, W, B, F>(p);
+#define SR_OCC(I, W, B, F) v[I] = occ<kForce, K, W, B, F, SINGLE>(p);
     SR_FORCE_VARIANTS(SR_OCC)
 #undef SR_OCC
-    const int c = occ<kForceCount, K, 8, 1, 0>(p), g = occ<kVjp, K, 8, 1, 0>(p);
+    const int c = occ<kForceCount, K, 8, 1, 0, SINGLE>(p), g = occ<kVjp, K, 8, 1, 0, SINGLE>(p);
     for (int i = 0; i < kVariants; ++i)
         if (v[i] < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
     if (c < 0 || g < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
@@ -552,23 +557,33 @@ int occupancy_k(sr_plan* p) {
     return SR_OK;
 }
 
-template <int K>
+template <int K, bool SINGLE>
 void launch_force_k(sr_plan* p, const Args& a, cudaStream_t st) {
     const int blocks = p->force_blocks_v[p->variant];
+    const VolDev& v0 = p->vols_h[0];
     switch (p->variant) {
 #define SR_LAUNCH(I, W, B, F) \
-    case I: k_pairs<kForce, K, W, B, F><<<blocks, W * 32, 0, st>>>(a); break;
+    case I: k_pairs<kForce, K, W, B, F, SINGLE><<<blocks, W * 32, 0, st>>>(a, v0); break;
         SR_FORCE_VARIANTS(SR_LAUNCH)
 #undef SR_LAUNCH
         default: break;
     }
 }
 
+template <int MODE, int K>
+void launch_mode(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
+    const VolDev& v0 = p->vols_h[0];
+    if (p->n_vol == 1) k_pairs<MODE, K, 8, 1, 0, true><<<blocks, kThreads, 0, st>>>(a, v0);
+    else k_pairs<MODE, K, 8, 1, 0, false><<<blocks, kThreads, 0, st>>>(a, v0);
+}
+
 }  // namespace
 
 // Pair-kernel variants selectable per plan (the autotuner times them).
 int force_occupancy(sr_plan* p) {
-    const int rc = p->chunk_k == 2 ? occupancy_k<2>(p) : occupancy_k<1>(p);
+    const bool single = p->n_vol == 1;
+    const int rc = p->chunk_k == 2 ? (single ? occupancy_k<2, true>(p) : occupancy_k<2, false>(p))
+                                   : (single ? occupancy_k<1, true>(p) : occupancy_k<1, false>(p));
     if (rc) return rc;
     p->force_blocks = p->force_blocks_v[p->variant];
     p->warps_per_block = kWarpsPerBlock;
@@ -596,13 +611,14 @@ int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_par
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->queue, 0, sizeof(long long), st));
     if (pairs || per_particle) {
         SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->evals, 0, 2 * sizeof(unsigned long long), st));
-        if (p->chunk_k == 2) k_pairs<kForceCount, 2, 8, 1, 0><<<p->count_blocks, kThreads, 0, st>>>(a);
-        else k_pairs<kForceCount, 1, 8, 1, 0><<<p->count_blocks, kThreads, 0, st>>>(a);
+        if (p->chunk_k == 2) launch_mode<kForceCount, 2>(p, a, p->count_blocks, st);
+        else launch_mode<kForceCount, 1>(p, a, p->count_blocks, st);
         SR_LAUNCH_CHECK("k_pairs<count>");
         return SR_OK;
     }
-    if (p->chunk_k == 2) launch_force_k<2>(p, a, st);
-    else launch_force_k<1>(p, a, st);
+    const bool single = p->n_vol == 1;
+    if (p->chunk_k == 2) { if (single) launch_force_k<2, true>(p, a, st); else launch_force_k<2, false>(p, a, st); }
+    else { if (single) launch_force_k<1, true>(p, a, st); else launch_force_k<1, false>(p, a, st); }
     SR_LAUNCH_CHECK("k_pairs<force>");
     return SR_OK;
 }
@@ -617,8 +633,8 @@ int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int 
     a.out = g_pos;
     a.accumulate = accumulate;
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->queue, 0, sizeof(long long), st));
-    if (p->chunk_k == 2) k_pairs<kVjp, 2, 8, 1, 0><<<p->vjp_blocks, kThreads, 0, st>>>(a);
-    else k_pairs<kVjp, 1, 8, 1, 0><<<p->vjp_blocks, kThreads, 0, st>>>(a);
+    if (p->chunk_k == 2) launch_mode<kVjp, 2>(p, a, p->vjp_blocks, st);
+    else launch_mode<kVjp, 1>(p, a, p->vjp_blocks, st);
     SR_LAUNCH_CHECK("k_pairs<vjp>");
     return SR_OK;
 }

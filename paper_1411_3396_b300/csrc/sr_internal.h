@@ -76,7 +76,7 @@ struct sr_plan {
     long long n_binned = 0;
     bool binned = false;
     int sub_bits = 6;
-    int chunk_k = 2;                       // particles per lane; chunk size = 32 * chunk_k
+    int chunk_k = 1;                       // particles per lane; chunk size = 32 * chunk_k
     int key_bits = 0;
     long long total_cells = 0;
     long long max_chunks = 0;
