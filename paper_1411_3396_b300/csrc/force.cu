@@ -539,8 +539,6 @@ int occ(sr_plan* p) {
     X(0, 8, 1, 0) X(1, 8, 2, 0) X(2, 8, 3, 0) X(3, 8, 4, 0) \
     X(4, 4, 6, 0) X(5, 4, 7, 0) X(6, 4, 8, 0) X(7, 8, 3, 1)
 
-int variant_warps_of(int v) { return (v >= 4 && v <= 6) ? 4 : 8; }
-
 template <int K, bool SINGLE>
 int occupancy_k(sr_plan* p) {
     int v[kVariants];
