@@ -236,6 +236,28 @@ int sr_invariants(sr_plan* plan, int64_t n, const float* vel, const float* acc, 
                   void* stream);
 
 /*
+ * sr_invariants_noalloc -- the same seven binary64 sums as sr_invariants
+ * (sum v, sum a, sum |v|^2 / 2 of n float4 rows; vel or acc may be NULL),
+ * for callers that cannot allocate device memory: no plan is needed and
+ * nothing is allocated per call.  The paper has no counterpart; this entry
+ * point exists for code that must not call cudaMalloc (an application whose
+ * allocator owns the device memory, or a monitoring hook inside a step loop
+ * that may neither allocate nor synchronise).
+ * Scratch: a fixed 224 KiB device array inside the library (one per device
+ * that loads it, held until the process exits), enough for n up to
+ * 67,108,864 rows; larger n fails with SR_ERR_CAPACITY.  The first call on
+ * each device looks up that array's device address (a CUDA runtime query),
+ * so make the first call on a device before any stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU (different
+ * streams, no ordering between them) race and may return wrong sums; calls
+ * on one stream are safe.  Every call rewrites all partial sums it reads.
+ * The summation order differs from sr_invariants, so results agree to
+ * rounding (about 1e-15 relative), not bit for bit.
+ * Errors: SR_ERR_ARG (null out, n < 0), SR_ERR_CAPACITY, SR_ERR_CUDA.
+ */
+int sr_invariants_noalloc(int64_t n, const float* vel, const float* acc, double* out, void* stream);
+
+/*
  * sr_plan_status -- synchronise the stream and report device-side flags of
  * the last calls: SR_ERR_RANGE if sr_bin saw a non-finite or out-of-range
  * position (the flag is then cleared), else SR_OK.

@@ -49,6 +49,7 @@ SIGNATURES = {
     "sr_kick": (c_int, [c_int64, c_void_p, c_void_p, c_float, c_void_p]),
     "sr_drift": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int64, c_void_p]),
     "sr_invariants": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sr_invariants_noalloc": (c_int, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sr_plan_status": (c_int, [c_void_p, c_void_p]),
     "sr_plan_copy": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p]),
     "sr_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),

@@ -16,7 +16,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libsr_b300.so"
-SOURCES = ["abi.cu", "fit.cpp", "radix.cu", "bin.cu", "force.cu", "plain.cu", "kick.cu"]
+SOURCES = ["abi.cu", "fit.cpp", "radix.cu", "bin.cu", "force.cu", "plain.cu", "kick.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
