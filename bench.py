@@ -377,7 +377,7 @@ def main():
     ap.add_argument("--workload", default="clustered256")
     ap.add_argument("--n-particles", type=int, default=0,
                     help="resize the workload (box scaled to keep density 1); 0 = as named")
-    ap.add_argument("--cpu-rows", type=int, default=2048)
+    ap.add_argument("--cpu-rows", type=int, default=24576)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
