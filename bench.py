@@ -176,14 +176,45 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(load))
 
 
-def make_inputs(name, n_particles=0):
+def shard_volumes(sizes, world, rank):
+    """Indices of the volumes rank `rank` evaluates: longest-first greedy
+    assignment of independent volumes to ranks by size (no data exchange)."""
+    loads = [0] * world
+    owner = {}
+    for v in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda k: (loads[k], k))
+        owner[v] = r
+        loads[r] += sizes[v]
+    return [v for v in range(len(sizes)) if owner[v] == rank]
+
+
+def reduce_over_ranks(pairs, ms, world, device):
+    """Whole-job pairs (sum over ranks) and step time (max over ranks)."""
+    if world == 1:
+        return pairs, ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return int(t.item()), float(m.item())
+
+
+def make_inputs(name, n_particles=0, world=1, rank=0):
+    """Volumes this rank evaluates: single-volume workloads are replicated
+    on every rank; a batch is sharded across ranks."""
     from workloads import configs as wc
     cfg = wc.resized(name, n_particles) if n_particles else wc.CONFIGS[name]
     w = wc.make_workload(cfg)
-    if len(w["volumes"]) != 1:
-        raise SystemExit("bench.py times single-volume workloads (uniform4k, zeldovich128, clustered256, diff64)")
-    (pos, box), = w["volumes"]
-    return cfg, pos, box, w["velocities"], w["params"]
+    vols = w["volumes"]
+    vel = w["velocities"]
+    if len(vols) > 1 and world > 1:
+        mine = shard_volumes([len(p) for p, _ in vols], world, rank)
+        starts = np.cumsum([0] + [len(p) for p, _ in vols])
+        vel = np.concatenate([vel[starts[v]:starts[v + 1]] for v in mine])
+        vols = [vols[v] for v in mine]
+    return cfg, vols, vel, w["params"]
 
 
 # ---------------------------------------------------------------------------
@@ -191,9 +222,10 @@ def make_inputs(name, n_particles=0):
 # ---------------------------------------------------------------------------
 
 def run_reference(args, rank, world):
-    cfg, pos, box, vel, prm = make_inputs(args.workload, args.n_particles)
+    cfg, vols, vel, prm = make_inputs(args.workload, args.n_particles)
     if rank != 0:
         return
+    pos, box = max(vols, key=lambda v: len(v[0]))
     cores = os.cpu_count() or 1
     total = args.warmup + args.steps
     rate, pairs, secs, per = cpu_oracle_sample(pos, box, prm, args.ref_rows, 7, cores, reps=total)
@@ -204,24 +236,30 @@ def run_reference(args, rank, world):
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n_particles": int(len(pos)), "box": box,
-                   "r_c": prm["rc"], "eps": prm["eps"], "sigma": prm["sigma"]},
+        "config": {"workload": args.workload, "n_particles": int(sum(len(p) for p, _ in vols)),
+                   "volumes": len(vols), "r_c": prm["rc"], "eps": prm["eps"], "sigma": prm["sigma"]},
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.ref_rows} random rows per step (FP64 k-d tree row sums; tree build untimed)"},
+                         "sample": f"{args.ref_rows} random rows per step of the largest volume "
+                                   "(FP64 k-d tree row sums; tree build untimed)"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_ours(args, rank, world, local_rank):
-    cfg, pos, box, vel_np, prm = make_inputs(args.workload, args.n_particles)
+    cfg, vols, vel_np, prm = make_inputs(args.workload, args.n_particles, world, rank)
+    pos = np.concatenate([p for p, _ in vols])
+    box = vols[0][1]
+    batch = len(vols) > 1 or cfg.get("kind") == "batch"
     n = len(pos)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
-        rate, pairs, secs, _ = cpu_oracle_sample(pos, box, prm, args.cpu_rows, 11, cores)
+        big_pos, big_box = max(vols, key=lambda v: len(v[0]))
+        rate, pairs, secs, _ = cpu_oracle_sample(big_pos, big_box, prm, args.cpu_rows, 11, cores)
         cpu = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_rows} random particles of the same workload, {pairs} pairs in {secs:.1f} s "
+               "sample": f"{args.cpu_rows} random particles of the same workload"
+                         f"{' (largest volume)' if batch else ''}, {pairs} pairs in {secs:.1f} s "
                          "(FP64 k-d tree row sums, tree build untimed)"}
 
     import torch
@@ -237,18 +275,31 @@ def run_ours(args, rank, world, local_rank):
     vel[:, :3] = torch.from_numpy(vel_np).to(dev).float()
     acc = torch.empty((n, 4), dtype=torch.float32, device=dev)
     inv = torch.empty(7, dtype=torch.float64, device=dev)
-    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n, n_cells=args.n_cells, sub_bits=args.sub_bits,
-                chunk_size=args.chunk_size)
+    if batch:
+        plan = Plan.batch([b for _, b in vols], [len(p) for p, _ in vols], prm["rc"], prm["eps"], prm["sigma"],
+                          sub_bits=args.sub_bits, chunk_size=args.chunk_size)
+    else:
+        plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n, n_cells=args.n_cells, sub_bits=args.sub_bits,
+                    chunk_size=args.chunk_size)
     dt = prm["dt"]
+    graph_stream = torch.cuda.Stream() if batch else None
 
     def step(ev=None):
-        plan.bin(x)
-        if ev is not None:
-            ev[0].record()
-        plan.force(acc)
-        if ev is not None:
-            ev[1].record()
-        kick(acc, vel, dt)
+        if batch:
+            # one captured graph: bin + persistent force + kick over all volumes
+            if ev is not None:
+                ev[0].record()
+            plan.graph_launch()
+            if ev is not None:
+                ev[1].record()
+        else:
+            plan.bin(x)
+            if ev is not None:
+                ev[0].record()
+            plan.force(acc)
+            if ev is not None:
+                ev[1].record()
+            kick(acc, vel, dt)
         plan.invariants(vel, acc, inv)
 
     # pair count of this configuration (binary32 predicate, counting variant)
@@ -265,6 +316,9 @@ def run_ours(args, rank, world, local_rank):
     ctr = plan.export("counters").cpu().numpy()
     evals, lane_evals = int(ctr[3]), int(ctr[4])
 
+    if batch:
+        torch.cuda.set_stream(graph_stream)
+        plan.graph_capture(x, vel, acc, dt)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -292,16 +346,13 @@ def run_ours(args, rank, world, local_rank):
     force_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     plan.status()
 
-    ms_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max = float(tt.item())
-    value = pairs * world / (ms_max * 1e-3)
+    pairs_all, ms_max = reduce_over_ranks(pairs, ms, world, dev)
+    value = pairs_all / (ms_max * 1e-3)
 
     # plain one-launch-per-slab kernel on the same binned input
     plain = None
     if not args.no_plain:
+        torch.cuda.set_stream(torch.cuda.default_stream())
         plan.bin(x)
         plan.force_plain(acc)
         torch.cuda.synchronize()
@@ -318,6 +369,7 @@ def run_ours(args, rank, world, local_rank):
     # end to end: pinned host buffers, H2D + step + D2H inside the timed region
     e2e = None
     if not args.no_e2e:
+        torch.cuda.set_stream(torch.cuda.default_stream())
         pos_h = torch.from_numpy(pos).pin_memory()
         vel_h = vel.cpu().pin_memory()
         acc_h = torch.empty((n, 4), dtype=torch.float32).pin_memory()
@@ -344,7 +396,9 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n_particles": n, "box": box, "r_c": prm["rc"],
+        "config": {"workload": args.workload, "n_particles": n, "volumes": len(vols),
+                   "box": box if not batch else [min(b for _, b in vols), max(b for _, b in vols)],
+                   "graph": bool(batch), "r_c": prm["rc"],
                    "eps": prm["eps"], "sigma": prm["sigma"], "dt": dt, "pairs_per_step": pairs,
                    "n_chunks": info["n_chunks"], "workers": info["workers"],
                    "variant": info["variant"], "autotune_ms": tune_ms, "chunk_size": info["chunk_size"],
@@ -352,7 +406,7 @@ def run_ours(args, rank, world, local_rank):
                    "in_range_fraction": pairs / max(evals, 1),
                    "lane_fill": evals / max(lane_evals, 1),
                    "l2": "inputs larger than L2 (402 MB positions); no flush",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+                   "parallelism": (f"sharded{world}" if batch else f"replicas{world}") if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "k_pairs<force>", "kernel_ms": force_ms,
