@@ -12,7 +12,7 @@ namespace sr {
 namespace {
 thread_local std::string g_last_error;
 
-int variant_warps(int v) { return (v >= 4 && v <= 6) ? 4 : 8; }
+int variant_warps(int v) { return (v >= 4 && v <= 6) || v == 10 ? 4 : 8; }
 std::atomic<long long> g_launches{0};
 
 constexpr double kSideMargin = 1.0 + 1.0 / (1 << 20);   // cell side must exceed r_c by this factor
@@ -443,6 +443,7 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
 
 int sr_plan_set_variant(sr_plan* p, int variant) {
     if (!p || variant < 0 || variant >= kVariants) return set_error(SR_ERR_ARG, "variant out of range");
+    if (p->force_blocks_v[variant] <= 0) return set_error(SR_ERR_ARG, "variant not available for this chunk size");
     p->variant = variant;
     p->force_blocks = p->force_blocks_v[variant];
     return SR_OK;
@@ -460,6 +461,8 @@ int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
     int best_v = p->variant;
     int rc = SR_OK;
     for (int v = 0; v < kVariants && rc == SR_OK; ++v) {
+        if (ms_out) ms_out[v] = 0.f;
+        if (p->force_blocks_v[v] <= 0) continue;       // not built for this chunk size
         p->variant = v;
         if ((rc = launch_force(p, acc, nullptr, nullptr, st))) break;   // warm-up
         cudaEventRecord(e0, st);

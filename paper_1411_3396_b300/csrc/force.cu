@@ -252,6 +252,79 @@ __device__ __forceinline__ void pair_vjp(const float4 q, const float4 gj, float 
     }
 }
 
+// Packed binary32 pairs (Blackwell f32x2 arithmetic): two values in one
+// 64-bit register pair, low half = even ring entry, high half = odd entry.
+// Each f32x2 operation is two IEEE binary32 operations (same rounding as the
+// scalar ones) in one instruction issue.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+struct PConsts {
+    f2 e2, n0, n1, n2, n3, n4, n5;
+    float rc2;
+};
+
+__device__ __forceinline__ PConsts pack_consts(const Consts& K) {
+    PConsts P;
+    P.e2 = f2_pack(K.eps2, K.eps2);
+    P.n0 = f2_pack(K.n0, K.n0); P.n1 = f2_pack(K.n1, K.n1); P.n2 = f2_pack(K.n2, K.n2);
+    P.n3 = f2_pack(K.n3, K.n3); P.n4 = f2_pack(K.n4, K.n4); P.n5 = f2_pack(K.n5, K.n5);
+    P.rc2 = K.rc2;
+    return P;
+}
+
+// Two ring entries against one particle; the same binary32 operations as
+// pair_force on each half.  An out-of-range pair contributes f = 0, and
+// fma(0, d, p) = p exactly, as the scalar path's skipped update.
+template <bool COUNT>
+__device__ __forceinline__ void pair_force2(f2 X, f2 Y, f2 Z, f2 XI, f2 YI, f2 ZI, const PConsts& P,
+                                            f2& PX, f2& PY, f2& PZ, int& npair) {
+    const f2 DX = f2_sub(X, XI), DY = f2_sub(Y, YI), DZ = f2_sub(Z, ZI);
+    f2 S = f2_fma(DX, DX, P.e2);
+    S = f2_fma(DY, DY, S);
+    S = f2_fma(DZ, DZ, S);
+    float s0, s1;
+    f2_unpack(S, s0, s1);
+    const f2 R = f2_pack(rsqrt_mufu(s0), rsqrt_mufu(s1));
+    const f2 R2 = f2_mul(R, R);
+    f2 H = f2_fma(P.n5, S, P.n4);
+    H = f2_fma(H, S, P.n3);
+    H = f2_fma(H, S, P.n2);
+    H = f2_fma(H, S, P.n1);
+    H = f2_fma(H, S, P.n0);
+    float f0, f1;
+    f2_unpack(f2_fma(R2, R, H), f0, f1);
+    const bool in0 = s0 < P.rc2, in1 = s1 < P.rc2;
+    const f2 F = f2_pack(in0 ? f0 : 0.f, in1 ? f1 : 0.f);
+    PX = f2_fma(F, DX, PX);
+    PY = f2_fma(F, DY, PY);
+    PZ = f2_fma(F, DZ, PZ);
+    if (COUNT) npair += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+}
+
 // Per-lane state: K active particles.
 template <int MODE, int K>
 struct WarpState {
@@ -265,24 +338,92 @@ struct WarpState {
 
 // FLAGS bit 0: two partial-sum sets (even / odd ring entries) to halve the
 // dependent FMA chain of the accumulation; summed before the Kahan update.
+// FLAGS bit 1: packed f32x2 pair loop over the pair-interleaved ring (see
+// ring_put); its partial sums split even / odd entries exactly like bit 0.
+template <int MODE, int K, int FLAGS>
+__device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, int base, int cnt,
+                                                 WarpState<MODE, K>& w, const PConsts& P) {
+    constexpr bool CNT = MODE == kForceCount;
+    const ulonglong2* A = reinterpret_cast<const ulonglong2*>(ring);
+    const f2* B = reinterpret_cast<const f2*>(ring + 32);
+    if (cnt & 1) {                                   // pad to an even count with an inert entry
+        const int p = (base + cnt) & (kRing - 1);
+        float* Af = reinterpret_cast<float*>(ring);
+        float* Bf = reinterpret_cast<float*>(ring + 32);
+        if ((threadIdx.x & 31) == 0) {
+            Af[(p >> 1) * 4 + (p & 1)] = kPad;
+            Af[(p >> 1) * 4 + 2 + (p & 1)] = kPad;
+            Bf[(p >> 1) * 2 + (p & 1)] = kPad;
+        }
+        __syncwarp();
+    }
+    const int m0 = base >> 1;
+    const int npairs = (cnt + 1) >> 1;
+    f2 XI[K], YI[K], ZI[K], PX[K], PY[K], PZ[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        XI[k] = f2_pack(w.x[k], w.x[k]);
+        YI[k] = f2_pack(w.y[k], w.y[k]);
+        ZI[k] = f2_pack(w.z[k], w.z[k]);
+        PX[k] = PY[k] = PZ[k] = 0ull;                // (+0, +0)
+    }
+    if (npairs == 16) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const ulonglong2 a = A[m0 + m];
+            const f2 z = B[m0 + m];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                pair_force2<CNT>(a.x, a.y, z, XI[k], YI[k], ZI[k], P, PX[k], PY[k], PZ[k], w.npair[k]);
+        }
+    } else {
+        for (int m = 0; m < npairs; ++m) {
+            const ulonglong2 a = A[m0 + m];
+            const f2 z = B[m0 + m];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                pair_force2<CNT>(a.x, a.y, z, XI[k], YI[k], ZI[k], P, PX[k], PY[k], PZ[k], w.npair[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float e, o;
+        f2_unpack(PX[k], e, o); kahan_add(w.sx[k], w.cx[k], e + o);
+        f2_unpack(PY[k], e, o); kahan_add(w.sy[k], w.cy[k], e + o);
+        f2_unpack(PZ[k], e, o); kahan_add(w.sz[k], w.cz[k], e + o);
+    }
+    if (MODE == kForceCount) w.nevals += cnt;
+}
+
 template <int MODE, int K, int FLAGS>
 __device__ __forceinline__ void run_batch(const float4* __restrict__ rp, const float4* __restrict__ rg, int cnt,
                                           WarpState<MODE, K>& w, const Consts& C) {
     float px[K], py[K], pz[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) px[k] = py[k] = pz[k] = 0.f;
-    if (MODE != kVjp && (FLAGS & 1) && cnt == 32) {
+    if (MODE != kVjp && (FLAGS & 1)) {
         constexpr bool CNT = MODE == kForceCount;
         float qx[K], qy[K], qz[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) qx[k] = qy[k] = qz[k] = 0.f;
+        if (cnt == 32) {
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-            const float4 a0 = rp[j], a1 = rp[j + 1];
+            for (int j = 0; j < 32; j += 2) {
+                const float4 a0 = rp[j], a1 = rp[j + 1];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                pair_force<CNT>(a0, w.x[k], w.y[k], w.z[k], C, px[k], py[k], pz[k], w.npair[k]);
-                pair_force<CNT>(a1, w.x[k], w.y[k], w.z[k], C, qx[k], qy[k], qz[k], w.npair[k]);
+                for (int k = 0; k < K; ++k) {
+                    pair_force<CNT>(a0, w.x[k], w.y[k], w.z[k], C, px[k], py[k], pz[k], w.npair[k]);
+                    pair_force<CNT>(a1, w.x[k], w.y[k], w.z[k], C, qx[k], qy[k], qz[k], w.npair[k]);
+                }
+            }
+        } else {
+            for (int j = 0; j < cnt; ++j) {
+                const float4 a0 = rp[j];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    if (j & 1) pair_force<CNT>(a0, w.x[k], w.y[k], w.z[k], C, qx[k], qy[k], qz[k], w.npair[k]);
+                    else pair_force<CNT>(a0, w.x[k], w.y[k], w.z[k], C, px[k], py[k], pz[k], w.npair[k]);
+                }
             }
         }
 #pragma unroll
@@ -345,6 +486,7 @@ __device__ __forceinline__ void run_batch(const float4* __restrict__ rp, const f
 template <int MODE, int K, int WARPS, int MINB, int FLAGS, bool SINGLE>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const VolDev v0) {
     constexpr int C = 32 * K;
+    constexpr bool PACKED = (FLAGS & 2) && MODE != kVjp;
     __shared__ float4 ring_p[WARPS][kRing];
     __shared__ float4 ring_g[MODE == kVjp ? WARPS : 1][kRing];
     const int warp = threadIdx.x >> 5;
@@ -362,6 +504,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
         const Item it = load_item(a, I);
         const VolDev& V = SINGLE ? v0 : a.vols[it.vol];
         const Consts KC = load_consts(V, MODE == kVjp);
+        const PConsts PK = PACKED ? pack_consts(KC) : PConsts{};
         WarpState<MODE, K> w;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -391,14 +534,25 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
                 const unsigned m = __ballot_sync(kFull, keep);
                 if (keep) {
                     const int slot = (w.wr + __popc(m & lt)) & (kRing - 1);
-                    rp[slot] = make_float4(xj, yj, zj, 0.f);
+                    if (PACKED) {
+                        // pair-interleaved ring: entry p -> x, y at float4 p/2 lanes
+                        // (p&1) and 2+(p&1); z in the second half at float2 p/2
+                        float* Af = reinterpret_cast<float*>(rp);
+                        float* Bf = reinterpret_cast<float*>(rp + 32);
+                        Af[(slot >> 1) * 4 + (slot & 1)] = xj;
+                        Af[(slot >> 1) * 4 + 2 + (slot & 1)] = yj;
+                        Bf[(slot >> 1) * 2 + (slot & 1)] = zj;
+                    } else {
+                        rp[slot] = make_float4(xj, yj, zj, 0.f);
+                    }
                     if (MODE == kVjp) rg[slot] = gjs[k];
                 }
                 w.wr += __popc(m);
                 __syncwarp();
                 if (w.wr - w.rd >= 32) {
                     const int base = w.rd & (kRing - 1);
-                    run_batch<MODE, K, FLAGS>(rp + base, rg + base, 32, w, KC);
+                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, base, 32, w, PK);
+                    else run_batch<MODE, K, FLAGS>(rp + base, rg + base, 32, w, KC);
                     w.rd += 32;
                     __syncwarp();
                 }
@@ -406,7 +560,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
         });
         if (w.wr > w.rd) {
             const int base = w.rd & (kRing - 1);
-            run_batch<MODE, K, FLAGS>(rp + base, rg + base, w.wr - w.rd, w, KC);
+            if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, base, w.wr - w.rd, w, PK);
+            else run_batch<MODE, K, FLAGS>(rp + base, rg + base, w.wr - w.rd, w, KC);
             __syncwarp();
         }
         int cpairs = 0;
@@ -535,19 +690,23 @@ int occ(sr_plan* p) {
 //   0: 8 x 1   1: 8 x 2   2: 8 x 3   3: 8 x 4   (register budgets 255, 128, 85, 64)
 //   4: 4 x 6   5: 4 x 7   6: 4 x 8              (85, 73, 64)
 //   7: 8 x 3 with split partial sums (even / odd neighbours)
+//   8..11: packed f32x2 pair loop (split partial sums): 8 x 2, 8 x 3, 4 x 6, 8 x 4
+// 64-particle chunks (K = 2) use variants 0..3 only.
 #define SR_FORCE_VARIANTS(X) \
     X(0, 8, 1, 0) X(1, 8, 2, 0) X(2, 8, 3, 0) X(3, 8, 4, 0) \
-    X(4, 4, 6, 0) X(5, 4, 7, 0) X(6, 4, 8, 0) X(7, 8, 3, 1)
+    X(4, 4, 6, 0) X(5, 4, 7, 0) X(6, 4, 8, 0) X(7, 8, 3, 1) \
+    X(8, 8, 2, 3) X(9, 8, 3, 3) X(10, 4, 6, 3) X(11, 8, 4, 3)
 
 template <int K, bool SINGLE>
 int occupancy_k(sr_plan* p) {
     int v[kVariants];
-#define SR_OCC(I, W, B, F) v[I] = occ<kForce, K, W, B, F, SINGLE>(p);
+#define SR_OCC(I, W, B, F) \
+    if constexpr (K == 1 || I < 4) v[I] = occ<kForce, K, W, B, F, SINGLE>(p); else v[I] = 0;
     SR_FORCE_VARIANTS(SR_OCC)
 #undef SR_OCC
     const int c = occ<kForceCount, K, 8, 1, 0, SINGLE>(p), g = occ<kVjp, K, 8, 1, 0, SINGLE>(p);
     for (int i = 0; i < kVariants; ++i)
-        if (v[i] < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
+        if (v[i] < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");   // 0 = not built for this K
     if (c < 0 || g < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
     for (int i = 0; i < kVariants; ++i) p->force_blocks_v[i] = v[i];
     p->count_blocks = c;
@@ -561,7 +720,7 @@ void launch_force_k(sr_plan* p, const Args& a, cudaStream_t st) {
     const VolDev& v0 = p->vols_h[0];
     switch (p->variant) {
 #define SR_LAUNCH(I, W, B, F) \
-    case I: k_pairs<kForce, K, W, B, F, SINGLE><<<blocks, W * 32, 0, st>>>(a, v0); break;
+    case I: if constexpr (K == 1 || I < 4) k_pairs<kForce, K, W, B, F, SINGLE><<<blocks, W * 32, 0, st>>>(a, v0); break;
         SR_FORCE_VARIANTS(SR_LAUNCH)
 #undef SR_LAUNCH
         default: break;

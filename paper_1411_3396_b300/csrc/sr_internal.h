@@ -18,7 +18,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBuckets = 1 << kRadixBits;
-constexpr int kVariants = 8;        // force-kernel variants (launch shape / accumulation)
+constexpr int kVariants = 12;       // force-kernel variants (launch shape / accumulation)
 
 // Per-volume constants, device resident, read once per work item.
 // Lengths inside kernels are in units of the fine grid h = L / (n_c 2^b).
@@ -123,7 +123,7 @@ struct sr_plan {
     int sm_count = 0;
     int variant = 0;                       // pair-kernel variant (launch bounds), see force.cu
     int force_blocks = 0;
-    int force_blocks_v[sr::kVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int force_blocks_v[sr::kVariants] = {};
     int vjp_blocks = 0;
     int count_blocks = 0;
     int warps_per_block = 8;               // of the selected force variant

@@ -80,19 +80,31 @@ def test_pair_counts_bit_exact(small_case):
 
 
 def test_all_kernel_variants_give_identical_forces(small_case):
-    # variants 0-6 share the summation order of the counting kernel; 7
-    # adds even and odd neighbours separately
+    # variants 0-6 share the summation order of the counting kernel; 7-11
+    # (scalar split sums and the packed two-wide loop) add even and odd
+    # neighbours separately and agree with each other bit for bit
+    from paper_1411_3396_b300 import SrError
     name, w, chunk = small_case
     plan, acc_c, _, _ = _gpu(w["volumes"], w["params"], count=True, chunk_size=chunk)
     ref = acc_c.tobytes()
-    for v in range(7):
+    first = range(7) if chunk == 32 else range(4)
+    for v in first:
         plan.set_variant(v)
         acc = to_np(plan.force())
         assert acc.tobytes() == ref, f"variant {v}"
-    plan.set_variant(7)
-    acc = to_np(plan.force())
+    if chunk == 64:
+        with pytest.raises(SrError):
+            plan.set_variant(8)
+        return
+    split = None
     a_ref, _ = oracle_force(w["volumes"], w["params"])
-    assert_force_close(acc, a_ref, f"{name} variant 7")
+    for v in range(7, 12):
+        plan.set_variant(v)
+        acc = to_np(plan.force())
+        if split is None:
+            split = acc
+            assert_force_close(acc, a_ref, f"{name} variant {v}")
+        assert acc.tobytes() == split.tobytes(), f"variant {v}"
 
 
 def test_plain_kernel_matches_oracle(small_case):
