@@ -422,6 +422,140 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
 
 
+VJP_FLOPS_PER_PAIR = 55   # d, s', r^2, r^3, q and q' (Horner), f, f', g_j - g_i, d.dg, w, two FMA per component
+
+
+def run_diff(args, rank, world, local_rank):
+    """Differentiable workload: one timed step = a 10-substep kick-drift
+    trajectory forward and its backward sweep (autograd over sr_force_vjp).
+    Metric: pair interactions per second, forward force pairs plus VJP
+    pairs (the same pair sets again in the backward sweep)."""
+    import torch
+
+    from paper_1411_3396_b300 import Plan, launch_count, trajectory
+    from workloads import configs as wc
+    from workloads import generators as gen
+
+    cfg = wc.resized("diff64", args.n_particles) if args.n_particles else wc.CONFIGS["diff64"]
+    box, n_side, steps, dt = cfg["box"], cfg["n_side"], cfg["steps"], cfg["dt"]
+    x0, psi = gen.zeldovich(n_side, box, cfg.get("rms", 0.5), cfg["seed"])
+    xt, _ = gen.zeldovich(n_side, box, cfg.get("rms", 0.5), cfg["seed"] + 1)
+    v0 = 0.1 * psi
+    n = len(x0)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    plan = Plan(box, cfg["rc"], cfg["eps"], cfg["sigma"], n, chunk_size=args.chunk_size)
+    xd = torch.from_numpy(x0).to(dev)
+    vd = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+    vd[:, :3] = torch.from_numpy(v0).to(dev).float()
+    target = torch.from_numpy(xt).to(dev)
+
+    def one(xi, vi):
+        x = xi.detach().clone().requires_grad_(True)
+        v = vi.detach().clone().requires_grad_(True)
+        xk, vk = trajectory(plan, x, v, steps, dt)
+        d = xk - target
+        d = d - box * torch.round(d / box)
+        loss = (d * d).sum()
+        loss.backward()
+        return loss, x.grad, v.grad
+
+    # pairs of every substep's configuration (counting kernel, untimed)
+    pairs = 0
+    with torch.no_grad():
+        x = xd.clone()
+        v = vd.clone()
+        acc = torch.empty_like(v)
+        from paper_1411_3396_b300 import kick
+        for _ in range(steps):
+            plan.bin(x)
+            _, pt, _ = plan.force(acc, count=True)
+            pairs += int(pt.item())
+            kick(acc, v, dt)
+            plan.drift(x, v, dt)
+    if args.variant >= 0:
+        plan.set_variant(args.variant)
+    else:
+        plan.bin(xd)
+        plan.autotune(reps=2)
+    for _ in range(args.warmup):
+        one(xd, vd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        loss, gx, gv = one(xd, vd)
+    e1.record()
+    torch.cuda.synchronize()
+    l1 = launch_count()
+    ms = e0.elapsed_time(e1) / args.steps
+    total_pairs = 2 * pairs
+    # kernel roofline on the initial configuration: force + VJP
+    plan.bin(xd)
+    g = torch.randn((n, 4), dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(2):
+        plan.force(acc)
+        plan.vjp(g)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(5):
+        plan.force(acc)
+    ev[1].record()
+    for _ in range(5):
+        plan.vjp(g)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_f = ev[0].elapsed_time(ev[1]) / 5
+    t_v = ev[1].elapsed_time(ev[2]) / 5
+    p0 = pairs / steps
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = p0 * (FLOPS_PER_PAIR + VJP_FLOPS_PER_PAIR) / ((t_f + t_v) * 1e-3) / 1e12
+    # end to end: H2D of x0, v0 from pinned memory, D2H of both gradients
+    x_h = torch.from_numpy(x0).pin_memory()
+    v_h = vd.cpu().pin_memory()
+    gx_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    gv_h = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        xi = x_h.to(dev, non_blocking=True)
+        vi = v_h.to(dev, non_blocking=True)
+        _, gx, gv = one(xi, vi)
+        gx_h.copy_(gx, non_blocking=True)
+        gv_h.copy_(gv, non_blocking=True)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    e2e_s = float(np.median(ts))
+    if rank != 0:
+        return
+    line = {
+        "metric": "short-range pair interactions/sec (FP32), forward + VJP of a differentiable trajectory",
+        "value": total_pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "diff64", "n_particles": n, "box": box, "substeps": steps, "dt": dt,
+                   "r_c": cfg["rc"], "eps": cfg["eps"], "sigma": cfg["sigma"],
+                   "pairs_forward": pairs, "pairs_per_step": total_pairs,
+                   "trajectories_per_s": 1e3 / ms, "loss": float(loss.item()),
+                   "parallelism": "single"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_pairs<force> + k_pairs<vjp> on x_0", "force_ms": t_f, "vjp_ms": t_v,
+                     "flops_per_pair": [FLOPS_PER_PAIR, VJP_FLOPS_PER_PAIR]},
+        "e2e": {"value": total_pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(n * (24 + 16)),
+                "d2h_bytes_per_step": int(n * (24 + 16)), "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": int(l1 - l0),
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -457,7 +591,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "diff64":
+        run_diff(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
