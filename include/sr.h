@@ -187,6 +187,30 @@ int sr_force(sr_plan* plan, float* acc, unsigned long long* pair_count,
              int* per_particle, void* stream);
 
 /*
+ * sr_force_kick -- sr_force with the kick fused into its epilogue: writes
+ * acc (device float4 rows, caller order) and applies vel += acc * dt to the
+ * same rows (device float4 rows, x, y, z; w untouched), with the
+ * arithmetic of sr_kick, so the result equals sr_force then sr_kick bit for
+ * bit, without re-reading acc.  The step either side of the pair sum in
+ * the paper's timestep (Sec. 2.1: the evolved active particles are
+ * updated).  Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG.
+ */
+int sr_force_kick(sr_plan* plan, float* acc, float* vel, float dt, void* stream);
+
+/*
+ * sr_leapfrog -- `steps` kick-drift-kick leapfrog steps of the short-range
+ * dynamics: per step v += a dt/2, x <- fold(x + v dt), re-bin, a = a(x),
+ * v += a dt/2.  Interior half kicks are merged (v += a dt in the fused
+ * force epilogue), so a step costs one drift, one sr_bin and one fused
+ * force-kick launch.  pos: device binary64 rows (updated); vel, acc:
+ * device float4 rows; acc must hold a(x) of the input positions (e.g. from
+ * sr_bin + sr_force) and holds a(x_K) on return.  n as for sr_bin.
+ * Errors: SR_ERR_ARG, SR_ERR_CAPACITY, SR_ERR_CUDA.
+ */
+int sr_leapfrog(sr_plan* plan, double* pos, float* vel, float* acc, double dt, int steps, int64_t n,
+                void* stream);
+
+/*
  * sr_force_plain -- the same accelerations from the plain kernel: one
  * launch per z-slab of cells, one thread per particle slot, neighbour
  * particles read straight from global memory over the 27 neighbour cells,
@@ -274,7 +298,7 @@ int sr_plan_copy(sr_plan* plan, int which, void* dst, int64_t bytes, void* strea
 /*
  * sr_step_host -- one whole step from host buffers (end-to-end form): copy
  * pos (host binary64 rows) and vel (host float4 rows) to plan-owned device
- * buffers, sr_bin, sr_force, sr_kick, copy acc (host float4 rows, nullable)
+ * buffers, sr_bin, sr_force_kick, copy acc (host float4 rows, nullable)
  * and the updated vel back, and wait for completion.  Host buffers should be
  * page-locked for overlap.  The first call allocates the staging buffers.
  */
@@ -311,8 +335,8 @@ int sr_plan_set_variant(sr_plan* plan, int variant);
 int sr_autotune(sr_plan* plan, float* acc, int reps, float* ms_out, void* stream);
 
 /*
- * sr_graph_capture -- record one whole step (sr_bin of pos, sr_force into
- * acc, sr_kick of vel by dt, for n particles) on stream into a CUDA graph
+ * sr_graph_capture -- record one whole step (sr_bin of pos, then
+ * sr_force_kick into acc and vel by dt, for n particles) on stream into a CUDA graph
  * owned by the plan, replacing any earlier one.  Nothing runs during the
  * capture.  pos, vel, acc: device buffers that every replay reads and
  * writes in place (refill their contents, keep the pointers).  stream must

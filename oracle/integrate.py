@@ -1,4 +1,5 @@
-"""Kick, drift, the kick-drift trajectory and its FP64 reverse mode.
+"""Kick, drift, the kick-drift trajectory and its FP64 reverse mode, and a
+kick-drift-kick leapfrog stepper.
 
 The paper's short-range timestep (Sec. 2.1) ends with the particles updated
 by the short-range force; the update is the kick v += a dt.  The
@@ -82,6 +83,20 @@ def loss_and_grad(x0, v0, x_target, box, rc, eps, c, dt, steps):
         vbar = vbar + dt * xbar                         # x_{k+1} = x_k + v_{k+1} dt
         xbar = xbar + force_vjp(xs[k], box, rc, eps, c, dt * vbar)   # v_{k+1} = v_k + a(x_k) dt
     return L, xbar, vbar
+
+
+def leapfrog(x0, v0, box, rc, eps, c, dt, steps, a0=None):
+    """Kick-drift-kick leapfrog: per step v += a dt/2; x = fold(x + v dt);
+    a = a(x); v += a dt/2.  Returns (x_K, v_K, a_K)."""
+    x = _wrap_for_tree(x0, box)
+    v = np.asarray(v0, np.float64).copy()
+    a = accel_kdtree(x, box, rc, eps, c)[0] if a0 is None else np.asarray(a0, np.float64)
+    for _ in range(steps):
+        v = kick(v, a, 0.5 * dt)
+        x = drift(x, v, dt, box)
+        a = accel_kdtree(x, box, rc, eps, c)[0]
+        v = kick(v, a, 0.5 * dt)
+    return x, v, a
 
 
 def invariants(v, a):

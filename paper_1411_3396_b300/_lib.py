@@ -45,6 +45,8 @@ SIGNATURES = {
     "sr_bin": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
     "sr_force": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sr_force_plain": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "sr_force_kick": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p]),
+    "sr_leapfrog": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_int64, c_void_p]),
     "sr_force_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_float, c_int, c_void_p]),
     "sr_kick": (c_int, [c_int64, c_void_p, c_void_p, c_float, c_void_p]),
     "sr_drift": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int64, c_void_p]),

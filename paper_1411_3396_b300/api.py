@@ -136,6 +136,24 @@ class Plan:
             return acc, pairs, pp
         return acc
 
+    def force_kick(self, acc: torch.Tensor, vel: torch.Tensor, dt: float):
+        """Accelerations with the kick fused into the epilogue (vel updated)."""
+        n = self._need_binned()
+        _need(acc, torch.float32, 4, "acc", n)
+        _need(vel, torch.float32, 4, "vel", n)
+        check(load().sr_force_kick(self._h, _ptr(acc), _ptr(vel), float(dt), _stream()))
+        return acc
+
+    def leapfrog(self, pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, dt: float, steps: int):
+        """KDK leapfrog steps in place; acc must hold a(pos) on entry."""
+        _need(pos, torch.float64, 3, "pos")
+        n = pos.shape[0]
+        _need(vel, torch.float32, 4, "vel", n)
+        _need(acc, torch.float32, 4, "acc", n)
+        check(load().sr_leapfrog(self._h, _ptr(pos), _ptr(vel), _ptr(acc), float(dt), int(steps), n, _stream()))
+        self.n = n
+        return pos, vel, acc
+
     def force_plain(self, acc: torch.Tensor | None = None):
         n = self._need_binned()
         if acc is None:

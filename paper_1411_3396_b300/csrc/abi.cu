@@ -344,6 +344,36 @@ int sr_force(sr_plan* p, float* acc, unsigned long long* pair_count, int* per_pa
     return launch_force(p, acc, pair_count, per_particle, as_stream(stream));
 }
 
+int sr_force_kick(sr_plan* p, float* acc, float* vel, float dt, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_kick before sr_bin");
+    if (!acc || !vel) return set_error(SR_ERR_ARG, "acc or vel is null");
+    return launch_force(p, acc, nullptr, nullptr, as_stream(stream), vel, dt);
+}
+
+int sr_leapfrog(sr_plan* p, double* pos, float* vel, float* acc, double dt, int steps, int64_t n, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!pos || !vel || !acc) return set_error(SR_ERR_ARG, "null buffer");
+    if (steps < 0) return set_error(SR_ERR_ARG, "steps must be >= 0");
+    if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    if (p->n_vol > 1 && n != p->capacity)
+        return set_error(SR_ERR_CAPACITY, "a batch plan steps exactly the sum of its volume counts");
+    if (steps == 0) return SR_OK;
+    cudaStream_t st = as_stream(stream);
+    const float half = (float)(0.5 * dt);
+    int rc = launch_kick(n, acc, vel, half, st);                  // opening half kick
+    for (int k = 0; k < steps && !rc; ++k) {
+        rc = launch_drift(p, pos, vel, dt, n, st);
+        if (!rc) rc = launch_bin(p, pos, n, st);
+        // interior half kicks merge: v += a dt, closing half kick on the last step
+        if (!rc) rc = launch_force(p, acc, nullptr, nullptr, st, vel, k + 1 < steps ? (float)dt : half);
+    }
+    if (rc) return rc;
+    p->n_binned = n;
+    p->binned = true;
+    return SR_OK;
+}
+
 int sr_force_plain(sr_plan* p, float* acc, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_plain before sr_bin");
@@ -433,8 +463,7 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
     SR_CUDA_CHECK(cudaMemcpyAsync(p->h_pos_dev, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     SR_CUDA_CHECK(cudaMemcpyAsync(p->h_vel_dev, vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, st));
     if ((rc = sr_bin(p, p->h_pos_dev, n, stream))) return rc;
-    if ((rc = launch_force(p, p->h_acc_dev, nullptr, nullptr, st))) return rc;
-    if ((rc = launch_kick(n, p->h_acc_dev, p->h_vel_dev, dt, st))) return rc;
+    if ((rc = launch_force(p, p->h_acc_dev, nullptr, nullptr, st, p->h_vel_dev, dt))) return rc;
     SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->h_vel_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
     if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
     SR_CUDA_CHECK(cudaStreamSynchronize(st));
@@ -493,8 +522,7 @@ int sr_graph_capture(sr_plan* p, const double* pos, float* vel, float* acc, floa
     cudaStream_t st = as_stream(stream);
     SR_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int rc = launch_bin(p, pos, n, st);
-    if (!rc) rc = launch_force(p, acc, nullptr, nullptr, st);
-    if (!rc) rc = launch_kick(n, acc, vel, dt, st);
+    if (!rc) rc = launch_force(p, acc, nullptr, nullptr, st, vel, dt);      // kick fused into the epilogue
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (rc) {

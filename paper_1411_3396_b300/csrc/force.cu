@@ -58,6 +58,8 @@ struct Args {
     int* per_particle;
     unsigned long long* pair_total;
     int accumulate;
+    float* vel;                       // force: nullable, fused kick vel += acc * kdt
+    float kdt;
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -580,6 +582,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
                 } else {
                     *dst = make_float4(ox, oy, oz, 0.f);
                 }
+                if (MODE != kVjp && a.vel) {                  // fused kick, same arithmetic as sr_kick
+                    float4* v = reinterpret_cast<float4*>(a.vel) + orig;
+                    float4 vv = *v;
+                    vv.x = fmaf(ox, a.kdt, vv.x);
+                    vv.y = fmaf(oy, a.kdt, vv.y);
+                    vv.z = fmaf(oz, a.kdt, vv.z);
+                    *v = vv;
+                }
                 if (MODE == kForceCount) {
                     if (a.per_particle) a.per_particle[orig] = w.npair[k] - 1;   // minus the self pair
                     cpairs += w.npair[k] - 1;
@@ -760,9 +770,12 @@ int launch_cost_and_order(sr_plan* p, cudaStream_t st) {
     return SR_OK;
 }
 
-int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_particle, cudaStream_t st) {
+int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_particle, cudaStream_t st,
+                 float* vel, float kdt) {
     Args a = make_args(p);
     a.out = acc;
+    a.vel = vel;
+    a.kdt = kdt;
     a.per_particle = per_particle;
     a.pair_total = pairs;
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->queue, 0, sizeof(long long), st));

@@ -167,7 +167,7 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st);
 // force, cost, order, vjp (force.cu)
 int launch_cost_and_order(sr_plan* p, cudaStream_t st);
 int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_particle,
-                 cudaStream_t st);
+                 cudaStream_t st, float* vel = nullptr, float kdt = 0.f);
 int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int accumulate,
                cudaStream_t st);
 int force_occupancy(sr_plan* p);

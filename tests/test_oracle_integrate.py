@@ -72,3 +72,24 @@ def test_kick_drift_basic():
     np.testing.assert_allclose(x, [[0.1, 7.8, 1.0]], atol=1e-12)
     inv = integrate.invariants(np.ones((4, 3)), np.zeros((4, 3)))
     assert inv["kinetic"] == 6.0 and np.all(inv["momentum"] == 4.0)
+
+
+def test_leapfrog_reversible_and_second_order(coef):
+    # leapfrog is time-reversible (run back with -dt) and its error shrinks
+    # by ~4x when dt halves (second order), against a fine-step reference
+    L = 8.0
+    x0, psi = gen.zeldovich(8, L, 0.5, 7)
+    v0 = 0.1 * psi
+    x1, v1, a1 = integrate.leapfrog(x0, v0, L, RC, EPS, coef, 0.01, 20)
+    xb, vb, _ = integrate.leapfrog(x1, -v1, L, RC, EPS, coef, 0.01, 20, a0=a1)
+    assert np.max(np.abs(force.min_image(xb - x0, L))) < 1e-10
+    assert np.max(np.abs(vb + v0)) < 1e-9
+    # order of accuracy in a smooth regime: a lattice with small displacements
+    xs, psis = gen.zeldovich(8, L, 0.05, 8)
+    T = 0.4
+    ref, _, _ = integrate.leapfrog(xs, 0.5 * psis, L, RC, EPS, coef, T / 256, 256)
+    errs = []
+    for k in (16, 32):
+        xk, _, _ = integrate.leapfrog(xs, 0.5 * psis, L, RC, EPS, coef, T / k, k)
+        errs.append(np.max(np.abs(force.min_image(xk - ref, L))))
+    assert 3.0 < errs[0] / errs[1] < 5.0
