@@ -422,6 +422,205 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
 
 
+MUFU_PER_SM_CLK = 16      # rsqrt results per SM per clock (measured on B300: 16; ex2 runs at 32)
+
+
+def _centers_inputs():
+    from workloads import configs as wc
+    w = wc.make_workload(wc.CONFIGS["clustered256"])
+    pos, box = w["volumes"][0]
+    return pos, box, w["labels"].astype(np.int32), len(w["halo_sizes"]), w["params"]["eps"]
+
+
+def cpu_centers_sample(pos, lab, box, eps, nh, budget, seed):
+    """Time the FP64 oracle's halo potentials on a seeded sample of whole
+    halos holding about `budget` ordered member pairs.  Returns
+    (unordered pairs/s, pairs, seconds, halos)."""
+    from oracle import centers as octr
+    rng = np.random.default_rng(seed)
+    sizes = np.bincount(lab[lab >= 0], minlength=nh).astype(np.int64)
+    pick, terms = [], 0
+    for h in rng.permutation(nh):
+        if sizes[h] < 2 or terms + sizes[h] ** 2 > budget:
+            continue
+        pick.append(h)
+        terms += int(sizes[h] ** 2)
+    sel = np.isin(lab, pick)
+    sub_pos, sub_lab = pos[sel], lab[sel]
+    remap = -np.ones(nh, np.int64)
+    remap[pick] = np.arange(len(pick))
+    sub_lab = remap[sub_lab]
+    t0 = time.perf_counter()
+    octr.halo_potentials(sub_pos, sub_lab, box, eps)
+    secs = time.perf_counter() - t0
+    pairs = int(np.sum(sizes[pick] * (sizes[pick] - 1) // 2))
+    return pairs / secs, pairs, secs, len(pick)
+
+
+def run_centers(args, rank, world, local_rank):
+    """Halo center finder on the 8,127 NFW halos of the clustered 256^3 set:
+    one step = sr_centers_run (sort by halo, member slots, symmetric pair
+    potential kernel, phi in caller order, per-halo argmin).  Metric:
+    unordered member pairs per second (sum over halos of N_h (N_h - 1) / 2
+    divided by the step time)."""
+    pos, box, lab, nh, eps = _centers_inputs()
+    n = len(pos)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        rate, cp, secs, nsel = cpu_centers_sample(pos, lab, box, eps, nh, args.cpu_center_terms, 11)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nsel} whole halos of the same catalogue, {cp} unordered pairs in {secs:.1f} s "
+                         "(FP64 NumPy blocked pair sums, one thread)"}
+
+    import torch
+
+    from paper_1411_3396_b300 import Centers, launch_count
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    xd = torch.from_numpy(pos).to(dev)
+    ld = torch.from_numpy(lab).to(dev)
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    cen = torch.empty(nh, dtype=torch.int64, device=dev)
+    cphi = torch.empty(nh, dtype=torch.float64, device=dev)
+    ctr = Centers(n, nh, "symmetric")
+
+    def step(ev=None):
+        ctr.prepare(xd, ld, nh, box, eps)
+        if ev is not None:
+            ev[0].record()
+        ctr.potential()
+        if ev is not None:
+            ev[1].record()
+        ctr.finish(phi, cen, cphi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = ctr.info()
+    pairs = int(info["pairs"])
+    uuid = str(getattr(props, "uuid", "")) if hasattr(props, "uuid") else ""
+    sampler = ClockSampler(uuid if rank == 0 else "")
+    if rank == 0 and not args.no_clocks:
+        sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    t_start.record()
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    l1 = launch_count()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
+    ms = t_start.elapsed_time(t_end) / args.steps
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    pairs_all, ms_max = reduce_over_ranks(pairs, ms, world, dev)
+
+    # plain gather kernel (thread per member, two rsqrt per unordered pair)
+    plain = None
+    if not args.no_plain:
+        ctr.set_variant("plain")
+        ctr.prepare(xd, ld, nh, box, eps)
+        ctr.potential()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctr.potential()
+        e1.record()
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        plain = {"ms": plain_ms, "pairs_per_s": pairs / (plain_ms * 1e-3),
+                 "speedup_of_symmetric_kernel": plain_ms / kern_ms}
+        ctr.set_variant("symmetric")
+
+    # end to end: positions and labels from pinned host memory, potentials
+    # and centers back to pinned host memory, inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(pos).pin_memory()
+        lab_h = torch.from_numpy(lab).pin_memory()
+        phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        cen_h = torch.empty(nh, dtype=torch.int64).pin_memory()
+        ts = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xd.copy_(pos_h, non_blocking=True)
+            ld.copy_(lab_h, non_blocking=True)
+            step()
+            phi_h.copy_(phi, non_blocking=True)
+            cen_h.copy_(cen, non_blocking=True)
+            torch.cuda.synchronize()
+            if k:
+                ts.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(ts))
+        e2e = {"value": pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(n * (24 + 4)),
+               "d2h_bytes_per_step": int(n * 8 + nh * 8), "ms_per_step": e2e_s * 1e3}
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = props.multi_processor_count * MUFU_PER_SM_CLK * sm_max * 1e6
+    achieved = pairs / (kern_ms * 1e-3)
+    if rank != 0:
+        ctr.close()
+        return
+    line = {
+        "metric": "halo center finding: unordered member pair potentials/sec (FP32, most-bound particle)",
+        "value": pairs_all / (ms_max * 1e-3), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "centers256", "catalogue": "clustered256 NFW halos", "n_particles": n,
+                   "n_members": info["n_members"], "n_halos": nh, "max_members": info["max_members"],
+                   "eps": eps, "box": box, "pairs_per_step": pairs, "evaluated_per_step": info["evaluated"],
+                   "items": info["items"], "fixed_shift": info["fixed_shift"],
+                   "l2": "inputs larger than L2 (402 MB positions); no flush",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "rsqrt/s (MUFU)",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_ctr_pairs", "kernel_ms": kern_ms,
+                     "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_SM_CLK} MUFU rsqrt/clk x "
+                                   f"{sm_max:.0f} MHz (rate measured by a probe; one rsqrt per unordered pair)"},
+        "plain": plain,
+        "e2e": e2e,
+        "gpu_launches": int(l1 - l0),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    ctr.close()
+
+
+def run_reference_centers(args, rank, world):
+    pos, box, lab, nh, eps = _centers_inputs()
+    if rank != 0:
+        return
+    per = []
+    for k in range(args.warmup + args.steps):
+        rate, cp, secs, nsel = cpu_centers_sample(pos, lab, box, eps, nh, args.cpu_center_terms // 16, 100 + k)
+        per.append(rate)
+    value = float(np.mean(per[args.warmup:]))
+    line = {
+        "impl": "reference",
+        "metric": "halo center finding: unordered member pair potentials/sec (FP32 path; oracle FP64)",
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "centers256", "catalogue": "clustered256 NFW halos", "n_particles": len(pos),
+                   "n_halos": nh, "eps": eps, "box": box},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step, a seeded sample of whole halos (FP64 NumPy blocked pair sums)"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 VJP_FLOPS_PER_PAIR = 55   # d, s', r^2, r^3, q and q' (Horner), f, f', g_j - g_i, d.dg, w, two FMA per component
 
 
@@ -568,6 +767,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=24576)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-center-terms", type=int, default=250_000_000,
+                    help="ordered member pairs in the oracle's center-finder sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -584,7 +785,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args, rank, world)
+            if args.workload == "centers256":
+                run_reference_centers(args, rank, world)
+            else:
+                run_reference(args, rank, world)
         return
     if world > 1:
         import torch
@@ -593,6 +797,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "diff64":
         run_diff(args, rank, world, local_rank)
+    elif args.workload == "centers256":
+        run_centers(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

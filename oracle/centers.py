@@ -58,3 +58,21 @@ def halo_centers(pos, labels, box, eps, n_halos):
             cphi[h] = phi[i]
             center[h] = i
     return center, cphi, phi
+
+
+def member_potentials(pos, labels, box, eps, idx):
+    """phi_i for the particles idx only (each summed over its own halo), for
+    checks of single outputs of large inputs."""
+    pos = np.asarray(pos, np.float64)
+    labels = np.asarray(labels)
+    out = np.zeros(len(idx))
+    e2 = eps * eps
+    for k, i in enumerate(np.asarray(idx)):
+        h = labels[i]
+        if h < 0:
+            continue
+        mem = np.flatnonzero(labels == h)
+        mem = mem[mem != i]
+        d = min_image(pos[mem] - pos[i], box)
+        out[k] = -np.sum(1.0 / np.sqrt(np.sum(d * d, axis=1) + e2))
+    return out

@@ -1,4 +1,5 @@
-"""ctypes declarations of the C ABI in include/sr.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/sr.h and include/sr_centers.h
+(argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -26,6 +27,13 @@ class SrPlanInfo(ctypes.Structure):
                 ("workers", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("chunk_size", ctypes.c_int32),
                 ("coef", c_double * 6)]
+
+
+class SrCentersInfo(ctypes.Structure):
+    _fields_ = [("n_particles", c_int64), ("n_members", c_int64), ("n_halos", c_int64),
+                ("max_members", c_int64), ("pairs", c_int64), ("items", c_int64),
+                ("evaluated", c_int64), ("fixed_shift", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("bad_labels", c_int64), ("wide_members", c_int64)]
 
 
 class SrError(RuntimeError):
@@ -59,6 +67,16 @@ SIGNATURES = {
     "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
     "sr_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
     "sr_graph_launch": (c_int, [c_void_p, c_void_p]),
+    "sr_centers_create": (c_int, [c_int64, ctypes.c_int32, POINTER(c_void_p)]),
+    "sr_centers_destroy": (c_int, [c_void_p]),
+    "sr_centers_set_variant": (c_int, [c_void_p, c_int]),
+    "sr_centers_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_int32, c_double, c_double,
+                               c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sr_centers_prepare": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, ctypes.c_int32, c_double,
+                                   c_double, c_void_p]),
+    "sr_centers_potential": (c_int, [c_void_p, c_void_p]),
+    "sr_centers_finish": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sr_centers_get_info": (c_int, [c_void_p, POINTER(SrCentersInfo)]),
     "sr_last_error": (c_char_p, []),
     "sr_launch_count": (c_int64, []),
 }

@@ -16,7 +16,8 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libsr_b300.so"
-SOURCES = ["abi.cu", "fit.cpp", "radix.cu", "bin.cu", "force.cu", "plain.cu", "kick.cu", "noalloc.cu"]
+SOURCES = ["abi.cu", "fit.cpp", "radix.cu", "bin.cu", "force.cu", "plain.cu", "kick.cu", "noalloc.cu",
+           "centers.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,7 +29,7 @@ def _nvcc() -> str:
 
 
 def _inputs():
-    files = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + [INCLUDE / "sr.h"]
+    files = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
     return files
 
 

@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads without a GPU, and exports every entry
-point include/sr.h declares; host-only entry points work on the CPU."""
+point the headers under include/ declare; host-only entry points and the
+argument checks that precede any device work behave on the CPU."""
 import ctypes
 import re
 from pathlib import Path
@@ -20,7 +21,7 @@ def lib():
 
 
 def declared_functions():
-    text = (ROOT / "include" / "sr.h").read_text()
+    text = "\n".join(p.read_text() for p in sorted((ROOT / "include").glob("*.h")))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sr_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
@@ -29,7 +30,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("sr_bin", "sr_force", "sr_kick", "sr_force_vjp", "sr_fit_poly",
-                 "sr_plan_create", "sr_plan_batch", "sr_plan_destroy", "sr_last_error"):
+                 "sr_plan_create", "sr_plan_batch", "sr_plan_destroy", "sr_last_error",
+                 "sr_centers_create", "sr_centers_run", "sr_centers_destroy"):
         assert must in names
 
 
@@ -68,3 +70,29 @@ def test_product_path_does_not_reference_the_oracle():
     for p in list(pkg.rglob("*.py")) + list(pkg.rglob("*.cu")) + list(pkg.rglob("*.cpp")) + \
             list(pkg.rglob("*.h")):
         assert "oracle" not in p.read_text(), p
+
+
+def test_centers_argument_checks_need_no_device(lib):
+    v = ctypes.c_void_p
+    create = lib.sr_centers_create
+    create.restype = ctypes.c_int
+    create.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(v)]
+    h = v()
+    assert create(0, 10, ctypes.byref(h)) == 1 and not h.value
+    assert create(100, 0, ctypes.byref(h)) == 1
+    assert create(1 << 31, 10, ctypes.byref(h)) == 1
+    assert create(100, 10, None) == 1
+    run = lib.sr_centers_run
+    run.restype = ctypes.c_int
+    run.argtypes = [v, v, v, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                    v, v, v, v]
+    assert run(None, None, None, 0, 0, 1.0, 0.1, None, None, None, None) == 1
+    lib.sr_centers_set_variant.restype = ctypes.c_int
+    lib.sr_centers_set_variant.argtypes = [v, ctypes.c_int]
+    assert lib.sr_centers_set_variant(None, 0) == 1
+    lib.sr_centers_get_info.restype = ctypes.c_int
+    lib.sr_centers_get_info.argtypes = [v, v]
+    assert lib.sr_centers_get_info(None, None) == 1
+    lib.sr_centers_destroy.restype = ctypes.c_int
+    lib.sr_centers_destroy.argtypes = [v]
+    assert lib.sr_centers_destroy(None) == 0

@@ -94,3 +94,11 @@ def test_block_size_and_member_order_do_not_matter():
     np.testing.assert_array_equal(perm[c2[ok]], c1[ok])
     phi3 = centers.halo_potentials(pos, lab, 20.0, 0.05, block=7)
     np.testing.assert_allclose(phi3, phi1, rtol=1e-12)
+
+
+def test_member_potentials_agree_with_full_sum():
+    pos, lab, sizes = gen.nfw_clustered(2000, 16.0, 21, m_lo=40.0, m_hi=500.0)
+    phi = centers.halo_potentials(pos, lab, 16.0, 0.05)
+    idx = np.random.default_rng(1).choice(len(pos), 50, replace=False)
+    np.testing.assert_allclose(centers.member_potentials(pos, lab, 16.0, 0.05, idx), phi[idx],
+                               rtol=1e-12)
