@@ -425,9 +425,10 @@ def run_ours(args, rank, world, local_rank):
 MUFU_PER_SM_CLK = 16      # rsqrt results per SM per clock (measured on B300: 16; ex2 runs at 32)
 
 
-def _centers_inputs():
+def _centers_inputs(n_particles=0):
     from workloads import configs as wc
-    w = wc.make_workload(wc.CONFIGS["clustered256"])
+    cfg = wc.resized("clustered256", n_particles) if n_particles else wc.CONFIGS["clustered256"]
+    w = wc.make_workload(cfg)
     pos, box = w["volumes"][0]
     return pos, box, w["labels"].astype(np.int32), len(w["halo_sizes"]), w["params"]["eps"]
 
@@ -463,7 +464,7 @@ def run_centers(args, rank, world, local_rank):
     potential kernel, phi in caller order, per-halo argmin).  Metric:
     unordered member pairs per second (sum over halos of N_h (N_h - 1) / 2
     divided by the step time)."""
-    pos, box, lab, nh, eps = _centers_inputs()
+    pos, box, lab, nh, eps = _centers_inputs(args.n_particles)
     n = len(pos)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -598,7 +599,7 @@ def run_centers(args, rank, world, local_rank):
 
 
 def run_reference_centers(args, rank, world):
-    pos, box, lab, nh, eps = _centers_inputs()
+    pos, box, lab, nh, eps = _centers_inputs(args.n_particles)
     if rank != 0:
         return
     per = []

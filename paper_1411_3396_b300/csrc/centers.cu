@@ -18,11 +18,12 @@
 // The symmetric kernel evaluates each unordered pair once and credits both
 // members; its cost is one MUFU rsqrt per unordered pair, and the MUFU unit
 // (16 results per clock per SM) bounds it.  A warp owns an I-tile of 128
-// members (4 per lane, packed two per f32x2 register) and streams 32-member
-// J blocks through shared memory; the I side accumulates in registers, the
-// J side per lane and is reduced across lanes through a padded shared
-// transpose once per block.  The plain kernel gives each member one thread
-// that sums over its whole halo (gather, two rsqrt per unordered pair).
+// members (4 per lane) and streams 32-member J blocks through shared memory;
+// arithmetic is packed (f32x2) over pairs of J members; the I side
+// accumulates in registers, the J side is written per lane to a padded
+// shared row and summed down the columns once per block.  The plain kernel
+// gives each member one thread that sums over its whole halo (gather, two
+// rsqrt per unordered pair).
 #include "sr_internal.h"
 #include "sr_centers.h"
 
@@ -36,7 +37,7 @@ constexpr int kTile = kBlk * kTileRows;
 constexpr int kJMax = 32;              // J blocks per work item
 constexpr int kWarps = 8;              // warps per block of the pair kernels
 constexpr int kThreads = kWarps * 32;
-constexpr int kRedStride = 36;         // padded row of the J-side transpose
+constexpr int kRedStride = 36;         // padded row of the J-side partial sums
 constexpr unsigned kFull = 0xffffffffu;
 
 struct CtrDev {
@@ -240,49 +241,57 @@ __global__ void k_ctr_zero(const unsigned long long* __restrict__ keys, const in
 __global__ void k_ctr_queue_reset(CtrDev* c) { c->queue = 0; }
 
 // -- 4a. symmetric pair kernel --------------------------------------------------
+// Shared memory of one warp: the J block as three coordinate rows, and the
+// J-side partial sums, one row of 32 per lane (row stride 36 floats: the
+// 16-byte stores of each quarter warp and the column reads are both free of
+// bank conflicts).
 struct WarpSmem {
-    float4 a[kBlk];                    // (x, x, y, y) of the J block
-    float2 b[kBlk];                    // (z, z)
-    float red[kBlk * kRedStride];      // J-side transpose
+    float x[kBlk], y[kBlk], z[kBlk];
+    float red[kBlk * kRedStride];
 };
 
-// One J member k against the lane's 4 I members; DIAG applies the
-// triangular mask of the tile's own blocks (pair kept iff slot_j > slot_i).
+// J members k and k+1 against the lane's 4 I members.  Arithmetic is packed
+// over the two J members: (x_k, x_k+1) - (x_i, x_i).  DIAG applies the
+// triangle of the tile's own blocks: with dr = q - 4t, I row r keeps the
+// whole block if r < dr, members k > lane if r == dr, nothing if r > dr.
 template <bool DIAG>
-__device__ __forceinline__ float pair_terms(const WarpSmem& sm, int k, f2 X01, f2 X23, f2 Y01, f2 Y23,
-                                            f2 Z01, f2 Z23, f2 E2, f2& P01, f2& P23, int lane, int dr) {
-    const float4 A = sm.a[k];
-    const float2 B = sm.b[k];
-    const f2 XJ = f2_pack(A.x, A.y), YJ = f2_pack(A.z, A.w), ZJ = f2_pack(B.x, B.y);
-    f2 DX = f2_sub(XJ, X01), DY = f2_sub(YJ, Y01), DZ = f2_sub(ZJ, Z01);
-    f2 S01 = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, E2)));
-    DX = f2_sub(XJ, X23); DY = f2_sub(YJ, Y23); DZ = f2_sub(ZJ, Z23);
-    f2 S23 = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, E2)));
-    f2 R01 = f2_rsqrt(S01), R23 = f2_rsqrt(S23);
-    if (DIAG) {
-        // row r < dr: whole block kept; r == dr: only k > lane; r > dr: none
-        const bool up = k > lane;
-        const float m0 = (0 < dr || (0 == dr && up)) ? 1.f : 0.f;
-        const float m1 = (1 < dr || (1 == dr && up)) ? 1.f : 0.f;
-        const float m2 = (2 < dr || (2 == dr && up)) ? 1.f : 0.f;
-        const float m3 = (3 < dr || (3 == dr && up)) ? 1.f : 0.f;
-        R01 = f2_mul(R01, f2_pack(m0, m1));
-        R23 = f2_mul(R23, f2_pack(m2, m3));
+__device__ __forceinline__ f2 pair_terms2(const WarpSmem& sm, int k, const f2 (&XI)[kTileRows],
+                                          const f2 (&YI)[kTileRows], const f2 (&ZI)[kTileRows], f2 E2,
+                                          f2 (&P)[kTileRows], int lane, int dr) {
+    const float2 X = *reinterpret_cast<const float2*>(&sm.x[k]);
+    const float2 Y = *reinterpret_cast<const float2*>(&sm.y[k]);
+    const float2 Z = *reinterpret_cast<const float2*>(&sm.z[k]);
+    const f2 XJ = f2_pack(X.x, X.y), YJ = f2_pack(Y.x, Y.y), ZJ = f2_pack(Z.x, Z.y);
+    f2 J = 0ull;
+#pragma unroll
+    for (int r = 0; r < kTileRows; ++r) {
+        const f2 DX = f2_sub(XJ, XI[r]), DY = f2_sub(YJ, YI[r]), DZ = f2_sub(ZJ, ZI[r]);
+        const f2 S = f2_fma(DZ, DZ, f2_fma(DY, DY, f2_fma(DX, DX, E2)));
+        f2 R = f2_rsqrt(S);
+        if (DIAG) {
+            const float m0 = (r < dr || (r == dr && k > lane)) ? 1.f : 0.f;
+            const float m1 = (r < dr || (r == dr && k + 1 > lane)) ? 1.f : 0.f;
+            R = f2_mul(R, f2_pack(m0, m1));
+        }
+        P[r] = f2_add(P[r], R);
+        J = r == 0 ? R : f2_add(J, R);
     }
-    P01 = f2_add(P01, R01);
-    P23 = f2_add(P23, R23);
-    float lo, hi;
-    f2_unpack(f2_add(R01, R23), lo, hi);
-    return lo + hi;
+    return J;
 }
 
 template <bool DIAG>
-__device__ __forceinline__ void block_terms(const WarpSmem& sm, float (&aj)[kBlk], f2 X01, f2 X23, f2 Y01,
-                                            f2 Y23, f2 Z01, f2 Z23, f2 E2, f2& P01, f2& P23, int lane,
+__device__ __forceinline__ void block_terms(WarpSmem& sm, const f2 (&XI)[kTileRows], const f2 (&YI)[kTileRows],
+                                            const f2 (&ZI)[kTileRows], f2 E2, f2 (&P)[kTileRows], int lane,
                                             int dr) {
+    // J pairs stay in registers until the block is done: stores into shared
+    // memory between the loads of the J rows would order every later load
+    // behind them
+    f2 Jb[kBlk / 2];
 #pragma unroll
-    for (int k = 0; k < kBlk; ++k)
-        aj[k] = pair_terms<DIAG>(sm, k, X01, X23, Y01, Y23, Z01, Z23, E2, P01, P23, lane, dr);
+    for (int k = 0; k < kBlk; k += 2) Jb[k >> 1] = pair_terms2<DIAG>(sm, k, XI, YI, ZI, E2, P, lane, dr);
+    ulonglong2* row = reinterpret_cast<ulonglong2*>(&sm.red[lane * kRedStride]);
+#pragma unroll
+    for (int m = 0; m < kBlk / 4; ++m) row[m] = make_ulonglong2(Jb[2 * m], Jb[2 * m + 1]);
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
@@ -297,7 +306,6 @@ k_ctr_pairs(const float4* __restrict__ slot_pos, unsigned long long* __restrict_
     const int n_rows = row0[nh];
     const int n_items = row_item0[n_rows];
     const f2 E2 = f2_pack(eps2, eps2);
-    const float4 padv = make_float4(sr::kPad, sr::kPad, sr::kPad, 0.f);
 
     while (true) {
         int item = 0;
@@ -323,44 +331,43 @@ k_ctr_pairs(const float4* __restrict__ slot_pos, unsigned long long* __restrict_
         const int q0 = kTileRows * t + (item - row_item0[lo]) * kJMax;
         const int q1 = min(q0 + kJMax, nb);
 
-        float4 xi[kTileRows];
+        f2 XI[kTileRows], YI[kTileRows], ZI[kTileRows], P[kTileRows];
+        long long acc[kTileRows];
 #pragma unroll
         for (int r = 0; r < kTileRows; ++r) {
             const int b = kTileRows * t + r;
-            xi[r] = b < nb ? slot_pos[base + (long long)b * kBlk + lane] : padv;
+            float4 v = make_float4(sr::kPad, sr::kPad, sr::kPad, 0.f);
+            if (b < nb) v = slot_pos[base + (long long)b * kBlk + lane];
+            XI[r] = f2_pack(v.x, v.x);
+            YI[r] = f2_pack(v.y, v.y);
+            ZI[r] = f2_pack(v.z, v.z);
+            acc[r] = 0;
         }
-        const f2 X01 = f2_pack(xi[0].x, xi[1].x), X23 = f2_pack(xi[2].x, xi[3].x);
-        const f2 Y01 = f2_pack(xi[0].y, xi[1].y), Y23 = f2_pack(xi[2].y, xi[3].y);
-        const f2 Z01 = f2_pack(xi[0].z, xi[1].z), Z23 = f2_pack(xi[2].z, xi[3].z);
-        long long acc[kTileRows] = {0, 0, 0, 0};
 
         float4 nxt = slot_pos[base + (long long)q0 * kBlk + lane];
         for (int q = q0; q < q1; ++q) {
             const float4 pj = nxt;
             if (q + 1 < q1) nxt = slot_pos[base + (long long)(q + 1) * kBlk + lane];
             __syncwarp();
-            sm.a[lane] = make_float4(pj.x, pj.x, pj.y, pj.y);
-            sm.b[lane] = make_float2(pj.z, pj.z);
+            sm.x[lane] = pj.x;
+            sm.y[lane] = pj.y;
+            sm.z[lane] = pj.z;
             __syncwarp();
-            f2 P01 = 0ull, P23 = 0ull;
-            float aj[kBlk];
+#pragma unroll
+            for (int r = 0; r < kTileRows; ++r) P[r] = 0ull;
             const int dr = q - kTileRows * t;
             if (dr < kTileRows)
-                block_terms<true>(sm, aj, X01, X23, Y01, Y23, Z01, Z23, E2, P01, P23, lane, dr);
+                block_terms<true>(sm, XI, YI, ZI, E2, P, lane, dr);
             else
-                block_terms<false>(sm, aj, X01, X23, Y01, Y23, Z01, Z23, E2, P01, P23, lane, dr);
+                block_terms<false>(sm, XI, YI, ZI, E2, P, lane, dr);
             // I side: this block's partials into the fixed-point registers
-            float p0, p1, p2, p3;
-            f2_unpack(P01, p0, p1);
-            f2_unpack(P23, p2, p3);
-            acc[0] += to_fixed(p0, scale);
-            acc[1] += to_fixed(p1, scale);
-            acc[2] += to_fixed(p2, scale);
-            acc[3] += to_fixed(p3, scale);
-            // J side: transpose through shared memory, lane k sums member k
-            float4* row = reinterpret_cast<float4*>(&sm.red[lane * kRedStride]);
 #pragma unroll
-            for (int k = 0; k < kBlk / 4; ++k) row[k] = make_float4(aj[4 * k], aj[4 * k + 1], aj[4 * k + 2], aj[4 * k + 3]);
+            for (int r = 0; r < kTileRows; ++r) {
+                float lo2, hi2;
+                f2_unpack(P[r], lo2, hi2);
+                acc[r] += to_fixed(lo2 + hi2, scale);
+            }
+            // J side: lane k sums column k of the warp's partial rows
             __syncwarp();
             float col = 0.f;
 #pragma unroll
