@@ -45,6 +45,7 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_PAIR = 28          # 3 sub, 3 fma (s'), 1 mul + 1 fma (r^3 - q), 5 fma Horner, 3 fma accumulate
 FP32_LANES_PER_SM = 128
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "force_clustered256.md")
+CENTERS_NOTE = os.path.join(ROOT, "profiles", "centers_clustered256.md")
 
 _CPU_STATE = {}
 
@@ -100,22 +101,22 @@ def measured_peaks():
     return {}
 
 
-def kernel_source_hash():
+def kernel_source_hash(names=("force.cu", "sr_internal.h")):
     h = hashlib.sha1()
-    for name in ("force.cu", "sr_internal.h"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_1411_3396_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
 
 
-def recorded_traffic():
-    """DRAM bytes per force launch from the committed ncu summary, or None
-    if the summary is missing or was taken on a different kernel source."""
-    if not os.path.exists(PROFILE_NOTE):
+def recorded_traffic(note=PROFILE_NOTE, names=("force.cu", "sr_internal.h")):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or
+    None if the summary is missing or was taken on a different kernel source."""
+    if not os.path.exists(note):
         return None
-    text = open(PROFILE_NOTE).read()
+    text = open(note).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_hash:\s*([0-9a-f]+)", text)
-    if not m or m.group(2) != kernel_source_hash():
+    if not m or m.group(2) != kernel_source_hash(names):
         return None
     return float(m.group(1))
 
@@ -585,7 +586,9 @@ def run_centers(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (402 MB positions); no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "rsqrt/s (MUFU)",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_ctr_pairs", "kernel_ms": kern_ms,
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic(CENTERS_NOTE, ("centers.cu",)) if not args.n_particles else None,
+                     "kernel": "k_ctr_pairs", "kernel_ms": kern_ms,
                      "peak_basis": f"{props.multi_processor_count} SMs x {MUFU_PER_SM_CLK} MUFU rsqrt/clk x "
                                    f"{sm_max:.0f} MHz (rate measured by a probe; one rsqrt per unordered pair)"},
         "plain": plain,
