@@ -1,5 +1,5 @@
-"""ctypes declarations of the C ABI in include/sr.h and include/sr_centers.h
-(argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/sr.h, include/sr_centers.h and
+include/sr_pm.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -77,6 +77,13 @@ SIGNATURES = {
     "sr_centers_potential": (c_int, [c_void_p, c_void_p]),
     "sr_centers_finish": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sr_centers_get_info": (c_int, [c_void_p, POINTER(SrCentersInfo)]),
+    "sr_pm_create": (c_int, [c_int, c_double, c_double, c_int64, POINTER(c_void_p)]),
+    "sr_pm_destroy": (c_int, [c_void_p]),
+    "sr_pm_deposit": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "sr_pm_power": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sr_pm_force": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]),
+    "sr_pm_fft": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    "sr_pm_copy": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "sr_last_error": (c_char_p, []),
     "sr_launch_count": (c_int64, []),
 }

@@ -1,0 +1,647 @@
+// Long-range side of the force split (Sec. 2: spectrally filtered PM on a
+// uniform grid) and the on-the-fly power spectrum (Sec. 4.1: CIC deposit,
+// FFT, |delta(k)|^2 binned in |k|, divided by the CIC window).
+//
+// Grid n^3 (n a power of two), [x][y][z] with z fastest, spacing D = L/n.
+//
+//   deposit   thread per particle: binary64 CIC weights of the 8 corners,
+//             added as 64-bit fixed point (2^S scale, no overflow for n_max
+//             particles in one cell), so the grid is independent of the
+//             order of the atomics;
+//   delta     counts / nbar - 1 into a binary32 complex grid;
+//   FFT       three passes, one per axis; a block loads T pencils of n
+//             points into shared memory in bit-reversed order (coalesced:
+//             along z for the z pass, T consecutive z columns for the y and
+//             x passes), runs log2(n) radix-2 butterfly stages with a
+//             twiddle table computed in binary64 on the host, and stores
+//             in natural order;
+//   P(k)      modes sorted once (at creation) by shell with the library's
+//             stable radix sort; each block sums a fixed segment of one
+//             shell in binary64 and a final pass adds a shell's segments in
+//             order: deterministic;
+//   force     a(k) = i k (4 pi / k^2) exp(-k^2 sigma^2) C(k) / W^2 for two
+//             components at once (a_x + i a_y is the transform of two real
+//             fields), inverse FFT, then a_z; CIC interpolation to the
+//             particles.
+#include "sr_internal.h"
+#include "sr_pm.h"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kFftSmemPoints = 4096;   // complex points per FFT block (32 KB)
+constexpr int kSegModes = 4096;        // modes per power-spectrum segment
+
+inline unsigned grid_for(long long n, int threads) {
+    return (unsigned)((n + threads - 1) / threads);
+}
+
+// Pencils per FFT block: up to kFftSmemPoints points, at most n (the y and
+// x passes take T consecutive z columns of one row).
+inline int fft_pencils(int n) {
+    const int t = kFftSmemPoints / n;
+    return t < 1 ? 1 : (t > n ? n : t);
+}
+
+inline size_t fft_smem(int n) {
+    return sizeof(float2) * ((size_t)n / 2 + (size_t)fft_pencils(n) * n);
+}
+
+__device__ __forceinline__ double fold(double v, double box) {
+    v = fmod(v, box);
+    if (v < 0.0) v += box;
+    if (v >= box) v = 0.0;
+    return v;
+}
+
+// Base cell and fractions of one particle.
+__device__ __forceinline__ void cic_cell(const double* __restrict__ pos, long long i, double box, double inv_d,
+                                         int n, int (&c)[3], double (&f)[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = fold(pos[3 * i + a], box) * inv_d;
+        const double fl = floor(u);
+        f[a] = u - fl;
+        long long ci = (long long)fl;
+        ci %= n;
+        c[a] = (int)ci;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cic_deposit(const double* __restrict__ pos, long long np, double box, double inv_d, int n, double scale,
+              unsigned long long* __restrict__ grid) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    int c[3];
+    double f[3];
+    cic_cell(pos, i, box, inv_d, n, c, f);
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+        const double wx = dx ? f[0] : 1.0 - f[0];
+        const long long ix = (c[0] + dx) % n;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const double wy = dy ? f[1] : 1.0 - f[1];
+            const long long iy = (c[1] + dy) % n;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const double wz = dz ? f[2] : 1.0 - f[2];
+                const long long iz = (c[2] + dz) % n;
+                const double w = wx * wy * wz;
+                atomicAdd(&grid[(ix * n + iy) * n + iz], (unsigned long long)llrint(w * scale));
+            }
+        }
+    }
+}
+
+// delta = counts / nbar - 1 as a complex grid (imaginary part 0).
+__global__ void k_pm_delta(const unsigned long long* __restrict__ fx, long long n3, double inv_scale,
+                           double inv_nbar, float2* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const double cnt = (double)(long long)fx[i] * inv_scale;
+    out[i] = make_float2((float)(cnt * inv_nbar - 1.0), 0.f);
+}
+
+__global__ void k_pm_counts(const unsigned long long* __restrict__ fx, long long n3, double inv_scale,
+                            double* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    out[i] = (double)(long long)fx[i] * inv_scale;
+}
+
+__device__ __forceinline__ unsigned bitrev(unsigned j, int logn) {
+    return __brev(j) >> (32 - logn);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// One FFT pass along `axis` (0 = x, stride n^2; 1 = y, stride n; 2 = z,
+// stride 1) over T pencils per block.  sign = -1 forward, +1 inverse.
+__global__ void __launch_bounds__(kThreads)
+k_fft_pass(float2* __restrict__ data, int n, int logn, int axis, int T, const float2* __restrict__ tw,
+           float sign) {
+    extern __shared__ float2 sm[];
+    float2* tws = sm;                         // n/2 twiddles
+    float2* buf = sm + n / 2;                 // T pencils of n points
+    const int half = n >> 1;
+    for (int k = threadIdx.x; k < half; k += blockDim.x) {
+        const float2 w = tw[k];
+        tws[k] = make_float2(w.x, sign < 0.f ? w.y : -w.y);
+    }
+    // pencil geometry
+    const long long nn = (long long)n * n;
+    long long base0;
+    long long pstride, estride;               // between the block's pencils, along a pencil
+    if (axis == 2) {
+        base0 = (long long)blockIdx.x * T * n;
+        pstride = n;
+        estride = 1;
+    } else {
+        const int per = n / T;
+        const long long outer = blockIdx.x / per;
+        const long long z0 = (long long)(blockIdx.x % per) * T;
+        base0 = (axis == 1 ? outer * nn : outer * n) + z0;
+        pstride = 1;
+        estride = axis == 1 ? n : nn;
+    }
+    const int total = T * n;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int q, j;
+        if (axis == 2) { q = idx / n; j = idx - q * n; }
+        else { j = idx / T; q = idx - j * T; }
+        buf[q * n + bitrev((unsigned)j, logn)] = data[base0 + q * pstride + j * estride];
+    }
+    __syncthreads();
+    const int bflies = T * half;
+    for (int s = 0; s < logn; ++s) {
+        const int h = 1 << s;
+        const int tstep = half >> s;          // twiddle index stride n / (2h)
+        for (int b = threadIdx.x; b < bflies; b += blockDim.x) {
+            const int q = b >> (logn - 1);
+            const int r = b & (half - 1);
+            const int i = r & (h - 1);
+            const int i0 = ((r >> s) << (s + 1)) + i;
+            float2* p = buf + q * n;
+            const float2 x0 = p[i0];
+            const float2 t = cmul(tws[i * tstep], p[i0 + h]);
+            p[i0] = make_float2(x0.x + t.x, x0.y + t.y);
+            p[i0 + h] = make_float2(x0.x - t.x, x0.y - t.y);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int q, j;
+        if (axis == 2) { q = idx / n; j = idx - q * n; }
+        else { j = idx / T; q = idx - j * T; }
+        data[base0 + q * pstride + j * estride] = buf[q * n + j];
+    }
+}
+
+// Shell of every mode (b = round(|m|); n/2 + 1 for modes outside 1..n/2)
+// as sort keys, the mode index as value.
+__global__ void k_pm_mode_keys(int n, long long n3, unsigned long long* __restrict__ keys, int* __restrict__ vals) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const int z = (int)(i % n), y = (int)((i / n) % n), x = (int)(i / ((long long)n * n));
+    const int h = n >> 1;
+    const long long mx = x < h ? x : x - n, my = y < h ? y : y - n, mz = z < h ? z : z - n;
+    const long long m2 = mx * mx + my * my + mz * mz;
+    const int b = (int)rint(sqrt((double)m2));
+    keys[i] = (unsigned long long)((b >= 1 && b <= h) ? b : h + 1);
+    vals[i] = (int)i;
+}
+
+// Per segment: sum of P and |k| over its modes (binary64, fixed order).
+__global__ void __launch_bounds__(kThreads)
+k_pm_power_seg(const float2* __restrict__ dk, const int* __restrict__ perm, const int* __restrict__ seg_start,
+               const int* __restrict__ seg_len, const double* __restrict__ sinc4, int n, double pnorm,
+               double kfund, double* __restrict__ psum, double* __restrict__ ksum) {
+    __shared__ double sp[kThreads], sk[kThreads];
+    const int s = blockIdx.x;
+    const int st = seg_start[s], len = seg_len[s];
+    const int h = n >> 1;
+    double ap = 0.0, ak = 0.0;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        const long long i = perm[st + t];
+        const int z = (int)(i % n), y = (int)((i / n) % n), x = (int)(i / ((long long)n * n));
+        const float2 v = dk[i];
+        const double p2 = (double)v.x * v.x + (double)v.y * v.y;
+        ap += pnorm * p2 / (sinc4[x] * sinc4[y] * sinc4[z]);
+        const double mx = x < h ? x : x - n, my = y < h ? y : y - n, mz = z < h ? z : z - n;
+        ak += kfund * sqrt(mx * mx + my * my + mz * mz);
+    }
+    sp[threadIdx.x] = ap;
+    sk[threadIdx.x] = ak;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sp[threadIdx.x] += sp[threadIdx.x + w];
+            sk[threadIdx.x] += sk[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        psum[s] = sp[0];
+        ksum[s] = sk[0];
+    }
+}
+
+// Per shell: add its segments in order.
+__global__ void k_pm_power_final(int nb, const int* __restrict__ bin_seg0, const int* __restrict__ bin_modes,
+                                 const double* __restrict__ psum, const double* __restrict__ ksum,
+                                 double* __restrict__ k_mean, double* __restrict__ power,
+                                 long long* __restrict__ modes) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double p = 0.0, k = 0.0;
+    for (int s = bin_seg0[b]; s < bin_seg0[b + 1]; ++s) {
+        p += psum[s];
+        k += ksum[s];
+    }
+    const long long m = bin_modes[b];
+    if (k_mean) k_mean[b] = m ? k / (double)m : NAN;
+    if (power) power[b] = m ? p / (double)m : NAN;
+    if (modes) modes[b] = m;
+}
+
+// Spectrum of two acceleration components packed as one complex field:
+// out = A_a(k) + i A_b(k), A(k) = i k G(k) C(k), C = nbar * delta_k, with
+// the inverse-transform normalisation 1/(n^3 D^3) folded in.  For a single
+// component pass b = -1.
+__global__ void k_pm_green(const float2* __restrict__ dk, int n, long long n3, float kf, float sig2,
+                           const float* __restrict__ inv_w2, float coef, int ca, int cb,
+                           float2* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const int z = (int)(i % n), y = (int)((i / n) % n), x = (int)(i / ((long long)n * n));
+    const int h = n >> 1;
+    const int mx = x < h ? x : x - n, my = y < h ? y : y - n, mz = z < h ? z : z - n;
+    const float kx = kf * mx, ky = kf * my, kz = kf * mz;
+    const float k2 = kx * kx + ky * ky + kz * kz;
+    if (i == 0) {
+        out[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    const float g = coef * expf(-k2 * sig2) / k2 * inv_w2[x] * inv_w2[y] * inv_w2[z];
+    const float gx = x == h ? 0.f : kx, gy = y == h ? 0.f : ky, gz = z == h ? 0.f : kz;
+    const float ka = ca == 0 ? gx : (ca == 1 ? gy : gz);
+    const float kb = cb == 0 ? gx : (cb == 1 ? gy : gz);
+    const float2 c = dk[i];
+    // i k_a g c = (-k_a g c.y, k_a g c.x)
+    const float2 A = make_float2(-ka * g * c.y, ka * g * c.x);
+    float2 r = A;
+    if (cb >= 0) {
+        const float2 B = make_float2(-kb * g * c.y, kb * g * c.x);
+        r = make_float2(A.x - B.y, A.y + B.x);   // A + i B
+    }
+    out[i] = r;
+}
+
+// Real (and imaginary) parts of the inverse transform into the float4
+// acceleration grid.
+__global__ void k_pm_extract(const float2* __restrict__ w, long long n3, int ca, int cb,
+                             float4* __restrict__ accg) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const float2 v = w[i];
+    float4 a = accg[i];
+    if (ca == 0) a.x = v.x; else if (ca == 1) a.y = v.x; else a.z = v.x;
+    if (cb == 0) a.x = v.y; else if (cb == 1) a.y = v.y; else if (cb == 2) a.z = v.y;
+    a.w = 0.f;
+    accg[i] = a;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cic_interp(const double* __restrict__ pos, long long np, double box, double inv_d, int n,
+             const float4* __restrict__ accg, float4* __restrict__ acc, int accumulate) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    int c[3];
+    double f[3];
+    cic_cell(pos, i, box, inv_d, n, c, f);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+        const double wx = dx ? f[0] : 1.0 - f[0];
+        const long long ix = (c[0] + dx) % n;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const double wy = dy ? f[1] : 1.0 - f[1];
+            const long long iy = (c[1] + dy) % n;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const double wz = dz ? f[2] : 1.0 - f[2];
+                const long long iz = (c[2] + dz) % n;
+                const double w = wx * wy * wz;
+                const float4 g = accg[(ix * n + iy) * n + iz];
+                ax += w * g.x;
+                ay += w * g.y;
+                az += w * g.z;
+            }
+        }
+    }
+    float4 o = accumulate ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    o.x += (float)ax;
+    o.y += (float)ay;
+    o.z += (float)az;
+    acc[i] = o;
+}
+
+}  // namespace
+
+struct sr_pm {
+    int n = 0;
+    int logn = 0;
+    long long n3 = 0;
+    double box = 0.0;
+    double sigma = 0.0;
+    long long n_max = 0;
+    int fixed_shift = 0;
+    unsigned long long* fx = nullptr;   // fixed-point CIC counts
+    float2* dk = nullptr;               // FFT of delta
+    float2* work = nullptr;             // inverse-transform scratch
+    float4* accg = nullptr;             // acceleration grid
+    float2* tw = nullptr;               // exp(-2 pi i k / n), k < n/2
+    double* sinc4 = nullptr;            // sinc^4(pi m / n) per axis index
+    float* inv_w2 = nullptr;            // 1 / sinc^4(pi m / n)
+    int* perm = nullptr;                // modes sorted by shell (shells 1..n/2 first)
+    int* seg_start = nullptr;
+    int* seg_len = nullptr;
+    int* bin_seg0 = nullptr;            // first segment of each shell (n/2 + 1)
+    int* bin_modes = nullptr;
+    double* psum = nullptr;
+    double* ksum = nullptr;
+    int n_seg = 0;
+    long long last_np = 0;
+    bool deposited = false;
+    bool accel_valid = false;
+};
+
+namespace {
+
+template <class T>
+int dalloc(T** p, long long count, const char* what) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+    if (e != cudaSuccess) return sr::cuda_fail(e, what);
+    return SR_OK;
+}
+
+int pm_free(sr_pm* p) {
+    void* bufs[] = {p->fx, p->dk, p->work, p->accg, p->tw, p->sinc4, p->inv_w2, p->perm, p->seg_start,
+                    p->seg_len, p->bin_seg0, p->bin_modes, p->psum, p->ksum};
+    for (void* b : bufs) cudaFree(b);
+    delete p;
+    return SR_OK;
+}
+
+int fft3(sr_pm* p, float2* data, float sign, cudaStream_t st) {
+    const int n = p->n;
+    const int T = fft_pencils(n);
+    const size_t smem = fft_smem(n);
+    const unsigned blocks = (unsigned)((long long)n * n / T);
+    for (int axis = 2; axis >= 0; --axis) {
+        k_fft_pass<<<blocks, kThreads, smem, st>>>(data, n, p->logn, axis, T, p->tw, sign);
+        SR_LAUNCH_CHECK("k_fft_pass");
+    }
+    return SR_OK;
+}
+
+// Mode permutation by shell and the segment tables (once, synchronous).
+int build_shells(sr_pm* p) {
+    const long long n3 = p->n3;
+    unsigned long long* keys[2] = {nullptr, nullptr};
+    int* vals[2] = {nullptr, nullptr};
+    sr::RadixScratch rs;
+    int rc = SR_OK;
+    for (int k = 0; k < 2 && !rc; ++k) {
+        rc = dalloc(&keys[k], n3, "sr_pm_create keys");
+        if (!rc) rc = dalloc(&vals[k], n3, "sr_pm_create vals");
+    }
+    if (!rc) rc = sr::radix_alloc(rs, n3);
+    int which = 0;
+    if (!rc) {
+        k_pm_mode_keys<<<grid_for(n3, kThreads), kThreads>>>(p->n, n3, keys[0], vals[0]);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = sr::cuda_fail(e, "k_pm_mode_keys");
+    }
+    int kb = 1;
+    while ((1 << kb) <= p->n / 2 + 1) ++kb;
+    if (!rc) rc = sr::radix_sort_pairs(keys, vals, (int)n3, kb, rs, nullptr, &which);
+    // modes per shell, counted on the host with the same classification
+    std::vector<int> modes(p->n / 2 + 2, 0);
+    if (!rc) {
+        const int n = p->n, h = n / 2;
+        std::vector<long long> sq(n);
+        for (int i = 0; i < n; ++i) {
+            const long long m = i < h ? i : i - n;
+            sq[i] = m * m;
+        }
+        for (int x = 0; x < n; ++x)
+            for (int y = 0; y < n; ++y)
+                for (int z = 0; z < n; ++z) {
+                    const int b = (int)std::rint(std::sqrt((double)(sq[x] + sq[y] + sq[z])));
+                    modes[(b >= 1 && b <= h) ? b : h + 1]++;
+                }
+    }
+    if (!rc) {
+        const int nb = p->n / 2;
+        std::vector<int> seg_start, seg_len, bin_seg0(nb + 1, 0);
+        long long off = 0;
+        for (int b = 1; b <= nb; ++b) {
+            bin_seg0[b - 1] = (int)seg_start.size();
+            for (int s = 0; s < modes[b]; s += kSegModes) {
+                seg_start.push_back((int)(off + s));
+                seg_len.push_back(std::min(kSegModes, modes[b] - s));
+            }
+            off += modes[b];
+        }
+        bin_seg0[nb] = (int)seg_start.size();
+        p->n_seg = (int)seg_start.size();
+        std::vector<int> bm(modes.begin() + 1, modes.begin() + 1 + nb);
+        rc = dalloc(&p->perm, n3, "sr_pm_create perm");
+        if (!rc) rc = dalloc(&p->seg_start, p->n_seg, "seg_start");
+        if (!rc) rc = dalloc(&p->seg_len, p->n_seg, "seg_len");
+        if (!rc) rc = dalloc(&p->bin_seg0, nb + 1, "bin_seg0");
+        if (!rc) rc = dalloc(&p->bin_modes, nb, "bin_modes");
+        if (!rc) rc = dalloc(&p->psum, p->n_seg, "psum");
+        if (!rc) rc = dalloc(&p->ksum, p->n_seg, "ksum");
+        cudaError_t e = cudaSuccess;
+        if (!rc) e = cudaMemcpy(p->perm, vals[which], sizeof(int) * n3, cudaMemcpyDeviceToDevice);
+        if (!rc && e == cudaSuccess)
+            e = cudaMemcpy(p->seg_start, seg_start.data(), sizeof(int) * p->n_seg, cudaMemcpyHostToDevice);
+        if (!rc && e == cudaSuccess)
+            e = cudaMemcpy(p->seg_len, seg_len.data(), sizeof(int) * p->n_seg, cudaMemcpyHostToDevice);
+        if (!rc && e == cudaSuccess)
+            e = cudaMemcpy(p->bin_seg0, bin_seg0.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice);
+        if (!rc && e == cudaSuccess) e = cudaMemcpy(p->bin_modes, bm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+        if (!rc && e != cudaSuccess) rc = sr::cuda_fail(e, "sr_pm_create tables");
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(keys[k]);
+        cudaFree(vals[k]);
+    }
+    sr::radix_free(rs);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sr_pm_create(int n_grid, double box, double sigma, int64_t n_max, sr_pm** out) {
+    if (!out) return sr::set_error(SR_ERR_ARG, "sr_pm_create: null out");
+    *out = nullptr;
+    int logn = 0;
+    while ((1 << logn) < n_grid) ++logn;
+    if (n_grid < 8 || n_grid > 1024 || (1 << logn) != n_grid)
+        return sr::set_error(SR_ERR_ARG, "sr_pm_create: n_grid must be a power of two in [8, 1024]");
+    if (!(box > 0.0) || !std::isfinite(box) || !(sigma >= 0.0) || !std::isfinite(sigma))
+        return sr::set_error(SR_ERR_ARG, "sr_pm_create: box must be > 0 and sigma >= 0");
+    if (n_max < 1 || n_max > 2147483647LL) return sr::set_error(SR_ERR_ARG, "sr_pm_create: bad n_max");
+    sr_pm* p = new sr_pm();
+    p->n = n_grid;
+    p->logn = logn;
+    p->n3 = (long long)n_grid * n_grid * n_grid;
+    p->box = box;
+    p->sigma = sigma;
+    p->n_max = n_max;
+    // no cell can hold more than n_max particles: n_max 2^S < 2^62
+    int bits = 0;
+    while ((1LL << bits) <= n_max) ++bits;
+    p->fixed_shift = 62 - bits;
+    if (p->fixed_shift > 52) p->fixed_shift = 52;
+    int rc = dalloc(&p->fx, p->n3, "sr_pm_create grid");
+    if (!rc) rc = dalloc(&p->dk, p->n3, "sr_pm_create dk");
+    if (!rc) rc = dalloc(&p->work, p->n3, "sr_pm_create work");
+    if (!rc) rc = dalloc(&p->accg, p->n3, "sr_pm_create accel grid");
+    if (!rc) rc = dalloc(&p->tw, n_grid / 2, "sr_pm_create twiddles");
+    if (!rc) rc = dalloc(&p->sinc4, n_grid, "sr_pm_create sinc");
+    if (!rc) rc = dalloc(&p->inv_w2, n_grid, "sr_pm_create window");
+    if (!rc) {
+        std::vector<float2> tw(n_grid / 2);
+        const double pi = 3.14159265358979323846;
+        for (int k = 0; k < n_grid / 2; ++k) {
+            const double a = -2.0 * pi * k / n_grid;
+            tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        std::vector<double> s4(n_grid);
+        std::vector<float> iw(n_grid);
+        for (int i = 0; i < n_grid; ++i) {
+            const int m = i < n_grid / 2 ? i : i - n_grid;
+            const double hh = pi * m / n_grid;
+            const double s = m == 0 ? 1.0 : std::sin(hh) / hh;
+            s4[i] = s * s * s * s;
+            iw[i] = (float)(1.0 / s4[i]);
+        }
+        cudaError_t e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->sinc4, s4.data(), sizeof(double) * n_grid, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->inv_w2, iw.data(), sizeof(float) * n_grid, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = sr::cuda_fail(e, "sr_pm_create tables");
+    }
+    if (!rc) {
+        const size_t smem = fft_smem(n_grid);
+        cudaError_t e = cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) rc = sr::cuda_fail(e, "sr_pm_create fft smem");
+    }
+    if (!rc) rc = build_shells(p);
+    if (rc) {
+        pm_free(p);
+        return rc;
+    }
+    *out = p;
+    return SR_OK;
+}
+
+int sr_pm_destroy(sr_pm* pm) {
+    if (!pm) return SR_OK;
+    return pm_free(pm);
+}
+
+int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream) {
+    if (!pm || !pos) return sr::set_error(SR_ERR_ARG, "sr_pm_deposit: null workspace or pos");
+    if (n < 1) return sr::set_error(SR_ERR_ARG, "sr_pm_deposit: n must be >= 1");
+    if (n > pm->n_max) return sr::set_error(SR_ERR_CAPACITY, "sr_pm_deposit: n above n_max");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double scale = std::ldexp(1.0, pm->fixed_shift);
+    SR_CUDA_CHECK(cudaMemsetAsync(pm->fx, 0, sizeof(unsigned long long) * (size_t)pm->n3, st));
+    k_cic_deposit<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box, pm->n,
+                                                              scale, pm->fx);
+    SR_LAUNCH_CHECK("k_cic_deposit");
+    const double inv_nbar = (double)pm->n3 / (double)n;
+    k_pm_delta<<<grid_for(pm->n3, kThreads), kThreads, 0, st>>>(pm->fx, pm->n3, 1.0 / scale, inv_nbar, pm->dk);
+    SR_LAUNCH_CHECK("k_pm_delta");
+    int rc = fft3(pm, pm->dk, -1.f, st);
+    if (rc) return rc;
+    pm->last_np = n;
+    pm->deposited = true;
+    pm->accel_valid = false;
+    return SR_OK;
+}
+
+int sr_pm_power(sr_pm* pm, double* k_mean, double* power, int64_t* modes, void* stream) {
+    if (!pm) return sr::set_error(SR_ERR_ARG, "sr_pm_power: null workspace");
+    if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_power: call sr_pm_deposit first");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double n6 = (double)pm->n3 * (double)pm->n3;
+    const double pnorm = pm->box * pm->box * pm->box / n6;
+    const double kf = 2.0 * 3.14159265358979323846 / pm->box;
+    k_pm_power_seg<<<pm->n_seg, kThreads, 0, st>>>(pm->dk, pm->perm, pm->seg_start, pm->seg_len, pm->sinc4, pm->n,
+                                                   pnorm, kf, pm->psum, pm->ksum);
+    SR_LAUNCH_CHECK("k_pm_power_seg");
+    const int nb = pm->n / 2;
+    k_pm_power_final<<<grid_for(nb, 128), 128, 0, st>>>(nb, pm->bin_seg0, pm->bin_modes, pm->psum, pm->ksum, k_mean,
+                                                        power, reinterpret_cast<long long*>(modes));
+    SR_LAUNCH_CHECK("k_pm_power_final");
+    return SR_OK;
+}
+
+int sr_pm_force(sr_pm* pm, const double* pos, int64_t n, float* acc, int accumulate, void* stream) {
+    if (!pm || !pos || !acc) return sr::set_error(SR_ERR_ARG, "sr_pm_force: null argument");
+    if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_force: call sr_pm_deposit first");
+    if (n < 1) return sr::set_error(SR_ERR_ARG, "sr_pm_force: n must be >= 1");
+    if (n > pm->n_max) return sr::set_error(SR_ERR_CAPACITY, "sr_pm_force: n above n_max");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!pm->accel_valid) {
+        const double d = pm->box / pm->n;
+        const double nbar = (double)pm->last_np / (double)pm->n3;
+        // C = nbar delta_k; a(x) = ifft(.) / D^3 = (1 / (n^3 D^3)) sum_k ...
+        const float coef = (float)(4.0 * 3.14159265358979323846 * nbar / ((double)pm->n3 * d * d * d));
+        const float kf = (float)(2.0 * 3.14159265358979323846 / pm->box);
+        const float sig2 = (float)(pm->sigma * pm->sigma);
+        const unsigned g = grid_for(pm->n3, kThreads);
+        k_pm_green<<<g, kThreads, 0, st>>>(pm->dk, pm->n, pm->n3, kf, sig2, pm->inv_w2, coef, 0, 1, pm->work);
+        SR_LAUNCH_CHECK("k_pm_green");
+        int rc = fft3(pm, pm->work, 1.f, st);
+        if (rc) return rc;
+        k_pm_extract<<<g, kThreads, 0, st>>>(pm->work, pm->n3, 0, 1, pm->accg);
+        SR_LAUNCH_CHECK("k_pm_extract");
+        k_pm_green<<<g, kThreads, 0, st>>>(pm->dk, pm->n, pm->n3, kf, sig2, pm->inv_w2, coef, 2, -1, pm->work);
+        SR_LAUNCH_CHECK("k_pm_green");
+        rc = fft3(pm, pm->work, 1.f, st);
+        if (rc) return rc;
+        k_pm_extract<<<g, kThreads, 0, st>>>(pm->work, pm->n3, 2, -1, pm->accg);
+        SR_LAUNCH_CHECK("k_pm_extract");
+        pm->accel_valid = true;
+    }
+    k_cic_interp<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box, pm->n,
+                                                             pm->accg, reinterpret_cast<float4*>(acc), accumulate);
+    SR_LAUNCH_CHECK("k_cic_interp");
+    return SR_OK;
+}
+
+int sr_pm_fft(sr_pm* pm, float* data, int inverse, void* stream) {
+    if (!pm || !data) return sr::set_error(SR_ERR_ARG, "sr_pm_fft: null argument");
+    return fft3(pm, reinterpret_cast<float2*>(data), inverse ? 1.f : -1.f, static_cast<cudaStream_t>(stream));
+}
+
+int sr_pm_copy(sr_pm* pm, int what, void* dst, void* stream) {
+    if (!pm || !dst) return sr::set_error(SR_ERR_ARG, "sr_pm_copy: null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (what == SR_PM_EXPORT_COUNTS || what == SR_PM_EXPORT_DELTA_K) {
+        if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_copy: nothing deposited");
+        if (what == SR_PM_EXPORT_COUNTS) {
+            k_pm_counts<<<grid_for(pm->n3, kThreads), kThreads, 0, st>>>(pm->fx, pm->n3,
+                                                                         std::ldexp(1.0, -pm->fixed_shift),
+                                                                         static_cast<double*>(dst));
+            SR_LAUNCH_CHECK("k_pm_counts");
+        } else {
+            SR_CUDA_CHECK(cudaMemcpyAsync(dst, pm->dk, sizeof(float2) * (size_t)pm->n3, cudaMemcpyDeviceToDevice, st));
+        }
+        return SR_OK;
+    }
+    if (what == SR_PM_EXPORT_ACCEL) {
+        if (!pm->accel_valid) return sr::set_error(SR_ERR_STATE, "sr_pm_copy: no acceleration grid yet");
+        SR_CUDA_CHECK(cudaMemcpyAsync(dst, pm->accg, sizeof(float4) * (size_t)pm->n3, cudaMemcpyDeviceToDevice, st));
+        return SR_OK;
+    }
+    return sr::set_error(SR_ERR_ARG, "sr_pm_copy: unknown selector");
+}
+
+}  // extern "C"

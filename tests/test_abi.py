@@ -96,3 +96,25 @@ def test_centers_argument_checks_need_no_device(lib):
     lib.sr_centers_destroy.restype = ctypes.c_int
     lib.sr_centers_destroy.argtypes = [v]
     assert lib.sr_centers_destroy(None) == 0
+
+
+def test_pm_argument_checks_need_no_device(lib):
+    v = ctypes.c_void_p
+    create = lib.sr_pm_create
+    create.restype = ctypes.c_int
+    create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(v)]
+    h = v()
+    assert create(100, 10.0, 0.8, 10, ctypes.byref(h)) == 1 and not h.value    # not a power of two
+    assert create(4, 10.0, 0.8, 10, ctypes.byref(h)) == 1                      # too small
+    assert create(2048, 10.0, 0.8, 10, ctypes.byref(h)) == 1                   # too large
+    assert create(64, -1.0, 0.8, 10, ctypes.byref(h)) == 1
+    assert create(64, 10.0, -0.5, 10, ctypes.byref(h)) == 1
+    assert create(64, 10.0, 0.8, 0, ctypes.byref(h)) == 1
+    for name, nargs in (("sr_pm_deposit", 4), ("sr_pm_power", 5), ("sr_pm_fft", 4), ("sr_pm_copy", 4)):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        assert f(*([None] * nargs)) == 1, name
+    lib.sr_pm_force.restype = ctypes.c_int
+    assert lib.sr_pm_force(None, None, ctypes.c_int64(0), None, 0, None) == 1
+    lib.sr_pm_destroy.restype = ctypes.c_int
+    assert lib.sr_pm_destroy(None) == 0

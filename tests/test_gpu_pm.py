@@ -1,0 +1,153 @@
+"""Long-range side (sr_pm_*) against the FP64 oracle: the FFT against a
+library FFT, CIC counts, delta(k), the CIC-compensated power spectrum and
+the PM accelerations element by element, plus conservation, accumulation,
+argument errors and the full 256^3 clustered set."""
+import numpy as np
+import pytest
+
+from oracle import pm as opm
+from workloads import configs as wc
+from workloads import generators as gen
+
+from helpers import rel_errors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# binary32 FFT: error relative to the transform's norm grows like
+# log2(n) * 2^-24; 3e-6 leaves margin up to n = 1024
+FFT_TOL = 3e-6
+# power per shell: binary32 delta_k against the FP64 oracle
+PK_TOL = 1e-4
+
+
+def _pm(ng, box, sigma, n):
+    from paper_1411_3396_b300 import PM
+    return PM(ng, box, sigma, n)
+
+
+@pytest.mark.parametrize("ng", [8, 16, 32, 64, 128])
+def test_fft_matches_library_fft(ng):
+    rng = np.random.default_rng(ng)
+    x = (rng.standard_normal((ng, ng, ng)) + 1j * rng.standard_normal((ng, ng, ng))).astype(np.complex64)
+    p = _pm(ng, float(ng), 0.8, 10)
+    d = torch.from_numpy(x).cuda()
+    p.fft(d)
+    ref = np.fft.fftn(x.astype(np.complex128))
+    got = d.cpu().numpy()
+    assert np.linalg.norm(got - ref) <= FFT_TOL * np.linalg.norm(ref)
+    p.fft(d, inverse=True)
+    back = d.cpu().numpy() / ng ** 3
+    assert np.linalg.norm(back - x) <= 2 * FFT_TOL * np.linalg.norm(x)
+    p.close()
+
+
+@pytest.fixture(scope="module")
+def clustered():
+    cfg = wc.small_variant("clustered256")
+    w = wc.make_workload(cfg)
+    (pos, box), = w["volumes"]
+    return pos, box
+
+
+@pytest.mark.parametrize("ng", [16, 32])
+def test_deposit_delta_k_and_power(clustered, ng):
+    pos, box = clustered
+    p = _pm(ng, box, 0.8, len(pos))
+    x = torch.from_numpy(pos).cuda()
+    p.deposit(x)
+    counts = p.export("counts").cpu().numpy()
+    ref = opm.cic_deposit(pos, box, ng)
+    assert np.max(np.abs(counts - ref)) <= 1e-9 * max(1.0, ref.max())
+    assert counts.sum() == pytest.approx(len(pos), rel=1e-12)
+    dk = p.export("delta_k").cpu().numpy()
+    dref = np.fft.fftn(ref / (len(pos) / ng ** 3) - 1.0)
+    assert np.linalg.norm(dk - dref) <= FFT_TOL * np.linalg.norm(dref)
+    k, pk, modes = (t.cpu().numpy() for t in p.power())
+    k_o, p_o, m_o = opm.power_spectrum(pos, box, ng)
+    np.testing.assert_array_equal(modes, m_o)
+    np.testing.assert_allclose(k, k_o, rtol=1e-12)
+    rel = np.abs(pk - p_o) / p_o
+    print(f"ng {ng}: P(k) rel err max {rel.max():.2e}")
+    assert rel.max() <= PK_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("ng", [16, 32])
+def test_pm_accelerations_match_oracle(clustered, ng):
+    pos, box = clustered
+    sigma = 0.8
+    p = _pm(ng, box, sigma, len(pos))
+    x = torch.from_numpy(pos).cuda()
+    p.deposit(x)
+    acc = p.force(x)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy()
+    ref = opm.pm_accel(pos, box, ng, sigma)
+    rel = rel_errors(a[:, :3].astype(np.float64), ref)
+    print(f"ng {ng}: PM accel rel err median {np.median(rel):.2e} max {rel.max():.2e}")
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4
+    assert np.all(a[:, 3] == 0.0)
+    # Newton's third law holds for the CIC deposit/interpolation pair
+    assert np.all(np.abs(a[:, :3].astype(np.float64).sum(axis=0)) <= 1e-5 * np.abs(a[:, :3]).sum())
+    grid = p.export("accel").cpu().numpy()[..., :3]
+    gref = opm.pm_accel_grid(opm.cic_deposit(pos, box, ng), box, sigma)
+    assert np.linalg.norm(grid - gref) <= 1e-5 * np.linalg.norm(gref)
+    # accumulate onto existing accelerations (e.g. the short-range ones)
+    base = torch.randn((len(pos), 4), dtype=torch.float32, device="cuda")
+    both = p.force(x, base.clone(), accumulate=True)
+    np.testing.assert_allclose(both.cpu().numpy()[:, :3], base.cpu().numpy()[:, :3] + a[:, :3], rtol=0,
+                               atol=1e-5 * np.abs(a).max() + 1e-6)
+    p.close()
+
+
+def test_lattice_on_grid_and_shot_noise():
+    # a lattice on the grid points has delta = 0; uniform points have the
+    # closed-form shot-noise level (checked against the oracle's value)
+    L, ng = 16.0, 16
+    lat = gen.lattice(16, L, offset=0.0)
+    p = _pm(ng, L, 0.8, len(lat))
+    p.deposit(torch.from_numpy(lat).cuda())
+    _, pk, _ = p.power()
+    assert float(pk.abs().max()) < 1e-10
+    acc = p.force(torch.from_numpy(lat).cuda())
+    assert float(acc.abs().max()) < 1e-4
+    p.close()
+
+
+def test_pm_state_and_argument_errors():
+    from paper_1411_3396_b300 import SrError
+    p = _pm(16, 16.0, 0.8, 100)
+    x = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(SrError):
+        p.power()                                         # nothing deposited yet
+    with pytest.raises(SrError):
+        p.force(x)
+    big = torch.zeros((101, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(SrError):
+        p.deposit(big)                                    # above n_max
+    p.close()
+
+
+def test_full_clustered_256_power_and_sampled_forces():
+    w = wc.make_workload(wc.CONFIGS["clustered256"])
+    (pos, box), = w["volumes"]
+    ng, sigma = 256, 0.8
+    p = _pm(ng, box, sigma, len(pos))
+    x = torch.from_numpy(pos).cuda()
+    p.deposit(x)
+    k, pk, modes = (t.cpu().numpy() for t in p.power())
+    acc = p.force(x).cpu().numpy()
+    p.close()
+    k_o, p_o, m_o = opm.power_spectrum(pos, box, ng)
+    np.testing.assert_array_equal(modes, m_o)
+    rel = np.abs(pk - p_o) / p_o
+    print(f"256^3: P(k) rel err max {rel.max():.2e}")
+    assert rel.max() <= PK_TOL
+    idx = np.random.default_rng(0).choice(len(pos), 20000, replace=False)
+    grid = opm.pm_accel_grid(opm.cic_deposit(pos, box, ng), box, sigma)
+    ref = opm.cic_interpolate(grid, pos[idx], box)
+    r = rel_errors(acc[idx, :3].astype(np.float64), ref)
+    print(f"256^3: sampled PM accel rel err median {np.median(r):.2e} max {r.max():.2e}")
+    assert np.median(r) <= 1e-5 and r.max() <= 1e-4
