@@ -601,6 +601,160 @@ def run_centers(args, rank, world, local_rank):
     ctr.close()
 
 
+def _pm_inputs(n_particles=0):
+    from workloads import configs as wc
+    cfg = wc.resized("clustered256", n_particles) if n_particles else wc.CONFIGS["clustered256"]
+    w = wc.make_workload(cfg)
+    (pos, box), = w["volumes"]
+    return pos, box, w["params"]["sigma"]
+
+
+def cpu_pm_sample(seed_n=128 ** 3):
+    """Time the FP64 oracle's long-range step (CIC deposit, FFT, P(k), PM
+    accelerations of every particle) on the clustered set resized to
+    seed_n particles and a seed_n grid.  Returns (particles/s, n, seconds)."""
+    from oracle import pm as opm
+    pos, box, sigma = _pm_inputs(seed_n)
+    ng = int(round(len(pos) ** (1.0 / 3.0)))
+    t0 = time.perf_counter()
+    opm.power_spectrum(pos, box, ng)
+    opm.pm_accel(pos, box, ng, sigma)
+    secs = time.perf_counter() - t0
+    return len(pos) / secs, len(pos), secs
+
+
+def run_pm(args, rank, world, local_rank):
+    """Long-range side on the clustered 256^3 set with a 256^3 mesh: one
+    step = sr_pm_deposit (CIC counts, delta, forward FFT) + sr_pm_power
+    (CIC-compensated P(k)) + sr_pm_force (filtered spectral accelerations,
+    two inverse FFTs, CIC interpolation to every particle).  Metric:
+    particles per second through the step."""
+    pos, box, sigma = _pm_inputs(args.n_particles)
+    n = len(pos)
+    ng = args.n_grid or int(round(n ** (1.0 / 3.0)))
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        rate, cn, secs = cpu_pm_sample()
+        cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": f"the same clustered catalogue resized to {cn} particles on a {round(cn ** (1 / 3))}^3 "
+                         f"mesh, whole step (deposit, FFT, P(k), accelerations) in {secs:.1f} s (FP64 NumPy)"}
+
+    import torch
+
+    from paper_1411_3396_b300 import PM, launch_count
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    x = torch.from_numpy(pos).to(dev)
+    acc = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    pm = PM(ng, box, sigma, n)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        pm.deposit(x)
+        if ev is not None:
+            ev[1].record()
+        k, p, m = pm.power()
+        if ev is not None:
+            ev[2].record()
+        pm.force(x, acc)
+        if ev is not None:
+            ev[3].record()
+        return k, p, m
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    uuid = str(getattr(props, "uuid", "")) if hasattr(props, "uuid") else ""
+    sampler = ClockSampler(uuid if rank == 0 else "")
+    if rank == 0 and not args.no_clocks:
+        sampler.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    t_start.record()
+    for kk in range(args.steps):
+        step(evs[kk])
+    t_end.record()
+    torch.cuda.synchronize()
+    l1 = launch_count()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
+    ms = t_start.elapsed_time(t_end) / args.steps
+    phases = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
+              for i, name in enumerate(("deposit_fft_ms", "power_ms", "force_ms"))}
+    n_all, ms_max = reduce_over_ranks(n, ms, world, dev)
+
+    # FFT pass against the HBM roofline: one forward transform (three
+    # passes, each reading and writing every complex64 point) timed alone
+    scratch = torch.randn((ng, ng, ng), dtype=torch.complex64, device=dev)
+    for _ in range(2):
+        pm.fft(scratch)
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        pm.fft(scratch)
+    e1.record()
+    torch.cuda.synchronize()
+    pass_ms = e0.elapsed_time(e1) / (3 * reps)
+    pass_bytes = 16 * ng ** 3
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(pos).pin_memory()
+        acc_h = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+        pk_h = torch.empty(ng // 2, dtype=torch.float64).pin_memory()
+        ts = []
+        for kk in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x.copy_(pos_h, non_blocking=True)
+            _, p, _ = step()
+            acc_h.copy_(acc, non_blocking=True)
+            pk_h.copy_(p, non_blocking=True)
+            torch.cuda.synchronize()
+            if kk:
+                ts.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(ts))
+        e2e = {"value": n / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": int(n * 24),
+               "d2h_bytes_per_step": int(n * 16 + (ng // 2) * 8), "ms_per_step": e2e_s * 1e3}
+    if rank != 0:
+        pm.close()
+        return
+    line = {
+        "metric": "long-range PM step (CIC deposit, FFT, P(k), filtered PM accelerations): particles/sec",
+        "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "pm256", "catalogue": "clustered256 particles", "n_particles": n, "n_grid": ng,
+                   "box": box, "sigma": sigma, **phases,
+                   "l2": "inputs larger than L2 (402 MB positions, 134 MB complex grid); no flush",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "k_fft_pass (one axis of a forward transform)",
+                     "kernel_ms": pass_ms, "bytes_per_launch": pass_bytes,
+                     "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": e2e,
+        "gpu_launches": int(l1 - l0),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    pm.close()
+
+
 def run_reference_centers(args, rank, world):
     pos, box, lab, nh, eps = _centers_inputs(args.n_particles)
     if rank != 0:
@@ -771,6 +925,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=24576)
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--n-grid", type=int, default=0, help="PM mesh points per axis (0 = cube root of n)")
     ap.add_argument("--cpu-center-terms", type=int, default=250_000_000,
                     help="ordered member pairs in the oracle's center-finder sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -803,6 +958,8 @@ def main():
         run_diff(args, rank, world, local_rank)
     elif args.workload == "centers256":
         run_centers(args, rank, world, local_rank)
+    elif args.workload == "pm256":
+        run_pm(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

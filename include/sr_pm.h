@@ -25,10 +25,11 @@
  *
  * Conventions are those of sr.h (status codes, sr_last_error(), caller-owned
  * device buffers, stream as void*, enqueue-only calls unless stated).
- * Numerics: CIC weights in binary64 summed as 64-bit fixed point (the
- * density grid does not depend on the order of the atomics), FFT and
- * k-space arithmetic in binary32 complex with binary64 twiddle tables,
- * power-spectrum sums in binary64 in a fixed order.
+ * Numerics: CIC cells and fractions in binary64, corner weights in
+ * binary32, summed as 64-bit fixed point (the density grid does not depend
+ * on the order of the atomics); FFT and k-space arithmetic in binary32
+ * complex with twiddle tables computed in binary64; power-spectrum terms in
+ * binary32 summed in binary64 in a fixed order.
  */
 #ifndef SR_PM_H
 #define SR_PM_H
@@ -50,7 +51,7 @@ typedef struct sr_pm sr_pm;
 
 /*
  * sr_pm_create -- workspace for an n_g^3 grid (n_g a power of two in
- * [8, 1024]) of a periodic box of side box, split scale sigma, for up to
+ * [16, 1024]) of a periodic box of side box, split scale sigma, for up to
  * n_max particles.  Device memory: about 48 n_g^3 bytes plus a mode
  * permutation built once here (it synchronises).
  * Errors: SR_ERR_ARG (bad n_g, box <= 0, sigma < 0, n_max < 1 or > 2^31-1),

@@ -4,21 +4,24 @@
 //
 // Grid n^3 (n a power of two), [x][y][z] with z fastest, spacing D = L/n.
 //
-//   deposit   thread per particle: binary64 CIC weights of the 8 corners,
-//             added as 64-bit fixed point (2^S scale, no overflow for n_max
-//             particles in one cell), so the grid is independent of the
-//             order of the atomics;
+//   deposit   thread per particle: cell and fraction in binary64, the 8
+//             corner weights in binary32, added as 64-bit fixed point (2^S
+//             scale, no overflow for n_max particles in one cell), so the
+//             grid is independent of the order of the atomics;
 //   delta     counts / nbar - 1 into a binary32 complex grid;
-//   FFT       three passes, one per axis; a block loads T pencils of n
-//             points into shared memory in bit-reversed order (coalesced:
-//             along z for the z pass, T consecutive z columns for the y and
-//             x passes), runs log2(n) radix-2 butterfly stages with a
-//             twiddle table computed in binary64 on the host, and stores
-//             in natural order;
+//   FFT       three passes, one per axis; n/16 threads per pencil, each
+//             holding 16 points in registers; Stockham stages of radix 16
+//             (then 2, 4 or 8 for the remaining factor) run in registers,
+//             with one padded shared-memory exchange between stages; the
+//             first stage reads and the last writes global memory in the
+//             same coalesced pattern (along z for the z pass, T consecutive
+//             z columns for the y and x passes); twiddles come from a table
+//             computed in binary64 on the host;
 //   P(k)      modes sorted once (at creation) by shell with the library's
-//             stable radix sort; each block sums a fixed segment of one
-//             shell in binary64 and a final pass adds a shell's segments in
-//             order: deterministic;
+//             stable radix sort; each block sums binary32 terms
+//             |delta_k|^2 / W^2 of a fixed segment of one shell in binary64
+//             and a final pass adds a shell's segments in order:
+//             deterministic; the mean |k| per shell is a table;
 //   force     a(k) = i k (4 pi / k^2) exp(-k^2 sigma^2) C(k) / W^2 for two
 //             components at once (a_x + i a_y is the transform of two real
 //             fields), inverse FFT, then a_z; CIC interpolation to the
@@ -32,67 +35,75 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kFftSmemPoints = 4096;   // complex points per FFT block (32 KB)
 constexpr int kSegModes = 4096;        // modes per power-spectrum segment
 
 inline unsigned grid_for(long long n, int threads) {
     return (unsigned)((n + threads - 1) / threads);
 }
 
-// Pencils per FFT block: up to kFftSmemPoints points, at most n (the y and
-// x passes take T consecutive z columns of one row).
+// Pencils per FFT block: 256 threads at n/16 threads per pencil, at most n
+// (the y and x passes take T consecutive z columns of one row).
 inline int fft_pencils(int n) {
-    const int t = kFftSmemPoints / n;
-    return t < 1 ? 1 : (t > n ? n : t);
+    const int t = kThreads / (n / 16);
+    return t > n ? n : t;
 }
 
 inline size_t fft_smem(int n) {
-    return sizeof(float2) * ((size_t)n / 2 + (size_t)fft_pencils(n) * n);
+    return sizeof(float2) * (size_t)fft_pencils(n) * (size_t)(n + n / 16);
 }
 
+// x mod L in [0, L) (fmod, then + L for a negative remainder, a result of
+// L itself to 0); inputs in [-L, 2L) take one exact
+// add or subtract, others the binary64 fmod.
 __device__ __forceinline__ double fold(double v, double box) {
-    v = fmod(v, box);
-    if (v < 0.0) v += box;
-    if (v >= box) v = 0.0;
+    if (v < 0.0 || v >= box) {
+        if (v >= -box && v < 2.0 * box) {
+            v = v < 0.0 ? v + box : v - box;
+        } else {
+            v = fmod(v, box);
+            if (v < 0.0) v += box;
+        }
+        if (v >= box) v = 0.0;
+    }
     return v;
 }
 
-// Base cell and fractions of one particle.
+// Base cell and binary32 fractions of one particle (the cell and the
+// fraction are formed in binary64; the weights that use the fraction run
+// in binary32).
 __device__ __forceinline__ void cic_cell(const double* __restrict__ pos, long long i, double box, double inv_d,
-                                         int n, int (&c)[3], double (&f)[3]) {
+                                         int n, int (&c)[3], float (&f)[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double u = fold(pos[3 * i + a], box) * inv_d;
         const double fl = floor(u);
-        f[a] = u - fl;
-        long long ci = (long long)fl;
-        ci %= n;
-        c[a] = (int)ci;
+        f[a] = (float)(u - fl);
+        int ci = (int)fl;
+        c[a] = ci >= n ? ci - n : ci;
     }
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_cic_deposit(const double* __restrict__ pos, long long np, double box, double inv_d, int n, double scale,
+k_cic_deposit(const double* __restrict__ pos, long long np, double box, double inv_d, int n, float scale,
               unsigned long long* __restrict__ grid) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     int c[3];
-    double f[3];
+    float f[3];
     cic_cell(pos, i, box, inv_d, n, c, f);
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-        const double wx = dx ? f[0] : 1.0 - f[0];
-        const long long ix = (c[0] + dx) % n;
+        const float wx = dx ? f[0] : 1.f - f[0];
+        const long long ix = c[0] + dx == n ? 0 : c[0] + dx;
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
-            const double wy = dy ? f[1] : 1.0 - f[1];
-            const long long iy = (c[1] + dy) % n;
+            const float wxy = wx * (dy ? f[1] : 1.f - f[1]);
+            const long long iy = c[1] + dy == n ? 0 : c[1] + dy;
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
-                const double wz = dz ? f[2] : 1.0 - f[2];
-                const long long iz = (c[2] + dz) % n;
-                const double w = wx * wy * wz;
-                atomicAdd(&grid[(ix * n + iy) * n + iz], (unsigned long long)llrint(w * scale));
+                const float w = wxy * (dz ? f[2] : 1.f - f[2]);
+                const long long iz = c[2] + dz == n ? 0 : c[2] + dz;
+                atomicAdd(&grid[(ix * n + iy) * n + iz], (unsigned long long)__float2ll_rn(w * scale));
             }
         }
     }
@@ -114,74 +125,191 @@ __global__ void k_pm_counts(const unsigned long long* __restrict__ fx, long long
     out[i] = (double)(long long)fx[i] * inv_scale;
 }
 
-__device__ __forceinline__ unsigned bitrev(unsigned j, int logn) {
-    return __brev(j) >> (32 - logn);
-}
-
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// One FFT pass along `axis` (0 = x, stride n^2; 1 = y, stride n; 2 = z,
-// stride 1) over T pencils per block.  sign = -1 forward, +1 inverse.
-__global__ void __launch_bounds__(kThreads)
-k_fft_pass(float2* __restrict__ data, int n, int logn, int axis, int T, const float2* __restrict__ tw,
-           float sign) {
-    extern __shared__ float2 sm[];
-    float2* tws = sm;                         // n/2 twiddles
-    float2* buf = sm + n / 2;                 // T pencils of n points
-    const int half = n >> 1;
-    for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        const float2 w = tw[k];
-        tws[k] = make_float2(w.x, sign < 0.f ? w.y : -w.y);
+// cos and sin of 2 pi q / 16, q = 0..7 (decimal expansions; q is a
+// compile-time constant at every use, so these fold into immediates).
+__device__ __forceinline__ constexpr float c16(int q) {
+    return q == 0 ? 1.f : q == 1 ? 0.92387953251128674f : q == 2 ? 0.70710678118654752f
+         : q == 3 ? 0.38268343236508977f : q == 4 ? 0.f : q == 5 ? -0.38268343236508977f
+         : q == 6 ? -0.70710678118654752f : -0.92387953251128674f;
+}
+__device__ __forceinline__ constexpr float s16(int q) {
+    return q == 0 ? 0.f : q == 1 ? 0.38268343236508977f : q == 2 ? 0.70710678118654752f
+         : q == 3 ? 0.92387953251128674f : q == 4 ? 1.f : q == 5 ? 0.92387953251128674f
+         : q == 6 ? 0.70710678118654752f : 0.38268343236508977f;
+}
+
+// x * exp(-+ 2 pi i q / 16), q = 0..15, with the trivial factors spelled out
+template <bool INV>
+__device__ __forceinline__ float2 rot16(int q, float2 x) {
+    if (q >= 8) {                                   // exp(-i pi) = -1
+        x = make_float2(-x.x, -x.y);
+        q -= 8;
     }
-    // pencil geometry
-    const long long nn = (long long)n * n;
-    long long base0;
-    long long pstride, estride;               // between the block's pencils, along a pencil
-    if (axis == 2) {
-        base0 = (long long)blockIdx.x * T * n;
-        pstride = n;
-        estride = 1;
+    if (q == 0) return x;
+    if (q == 4) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    const float c = c16(q), sn = INV ? s16(q) : -s16(q);
+    return make_float2(fmaf(c, x.x, -sn * x.y), fmaf(c, x.y, sn * x.x));
+}
+
+// 4-point DFT in place on (a, b, c, d) = x[0], x[1], x[2], x[3].
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
+    const float2 t0 = make_float2(a.x + c.x, a.y + c.y), t1 = make_float2(a.x - c.x, a.y - c.y);
+    const float2 t2 = make_float2(b.x + d.x, b.y + d.y), t3 = make_float2(b.x - d.x, b.y - d.y);
+    // forward: X1 = t1 - i t3, X3 = t1 + i t3 (inverse: the other way)
+    const float2 it3 = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);
+    a = make_float2(t0.x + t2.x, t0.y + t2.y);
+    c = make_float2(t0.x - t2.x, t0.y - t2.y);
+    b = make_float2(t1.x + it3.x, t1.y + it3.y);
+    d = make_float2(t1.x - it3.x, t1.y - it3.y);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = make_float2(t.x + b.x, t.y + b.y);
+    b = make_float2(t.x - b.x, t.y - b.y);
+}
+
+// In-register R-point DFT (R = 2, 4, 8, 16) on v[u + m G], m < R, G = 16/R,
+// output in natural order in the same registers.  R = 16 and 8 are split
+// as 4 x 4 and 2 x 4 (inner DFTs over the stride-4 or stride-2 subsets,
+// twiddles W_R^{n2 k1}, outer DFTs).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2 (&v)[16], int u) {
+    constexpr int G = 16 / R;
+    if constexpr (R == 2) {
+        dft2<INV>(v[u], v[u + G]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[u], v[u + G], v[u + 2 * G], v[u + 3 * G]);
+    } else if constexpr (R == 8) {
+        // x[n2 + 2 n1], n2 < 2, n1 < 4 -> y[n2][k1] -> X[k1 + 4 k2]
+        float2 y[2][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 2; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[u + (n2 + 2 * n1) * G];
+            dft4<INV>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            y[1][k1] = rot16<INV>(2 * k1, y[1][k1]);     // W8^{k1} = W16^{2 k1}
+            dft2<INV>(y[0][k1], y[1][k1]);
+            v[u + k1 * G] = y[0][k1];
+            v[u + (k1 + 4) * G] = y[1][k1];
+        }
     } else {
-        const int per = n / T;
-        const long long outer = blockIdx.x / per;
-        const long long z0 = (long long)(blockIdx.x % per) * T;
-        base0 = (axis == 1 ? outer * nn : outer * n) + z0;
-        pstride = 1;
-        estride = axis == 1 ? n : nn;
+        float2 y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[u + n2 + 4 * n1];
+            dft4<INV>(y[n2][0], y[n2][1], y[n2][2], y[n2][3]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            y[1][k1] = rot16<INV>(k1, y[1][k1]);
+            y[2][k1] = rot16<INV>(2 * k1, y[2][k1]);
+            y[3][k1] = rot16<INV>((3 * k1) & 15, y[3][k1]);
+            dft4<INV>(y[0][k1], y[1][k1], y[2][k1], y[3][k1]);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[u + k1 + 4 * k2] = y[k2][k1];
+        }
     }
-    const int total = T * n;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int q, j;
-        if (axis == 2) { q = idx / n; j = idx - q * n; }
-        else { j = idx / T; q = idx - j * T; }
-        buf[q * n + bitrev((unsigned)j, logn)] = data[base0 + q * pstride + j * estride];
+}
+
+// Stockham stage of radix R at stride S on a length-N transform: register
+// v[e] holds element t + e N/16; butterfly j = t + u N/16 (u < 16/R) takes
+// elements j + m N/R (registers u + m 16/R), multiplies by
+// W_{S R}^{(j mod S) m}, and its output m belongs at
+// (j / S) S R + (j mod S) + m S.
+template <int N, int R, int S, bool INV>
+__device__ __forceinline__ void fft_stage(float2 (&v)[16], int t, const float2* __restrict__ tw) {
+    constexpr int G = 16 / R;
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+        if (S > 1) {
+            const int p = (t + u * (N / 16)) & (S - 1);
+#pragma unroll
+            for (int m = 1; m < R; ++m) {
+                float2 w = __ldg(&tw[p * m * (N / (S * R))]);
+                if (INV) w.y = -w.y;
+                v[u + m * G] = cmul(w, v[u + m * G]);
+            }
+        }
+        dft_r<R, INV>(v, u);
+    }
+}
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// Outputs of stage (R, S) to shared memory, then element t + e N/16 back
+// into register e.
+template <int N, int R, int S>
+__device__ __forceinline__ void exchange(float2 (&v)[16], int t, float2* __restrict__ buf) {
+    constexpr int G = 16 / R;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+        const int j = t + u * (N / 16);
+        const int base = (j / S) * S * R + (j & (S - 1));
+#pragma unroll
+        for (int m = 0; m < R; ++m) buf[pad16(base + m * S)] = v[u + m * G];
     }
     __syncthreads();
-    const int bflies = T * half;
-    for (int s = 0; s < logn; ++s) {
-        const int h = 1 << s;
-        const int tstep = half >> s;          // twiddle index stride n / (2h)
-        for (int b = threadIdx.x; b < bflies; b += blockDim.x) {
-            const int q = b >> (logn - 1);
-            const int r = b & (half - 1);
-            const int i = r & (h - 1);
-            const int i0 = ((r >> s) << (s + 1)) + i;
-            float2* p = buf + q * n;
-            const float2 x0 = p[i0];
-            const float2 t = cmul(tws[i * tstep], p[i0 + h]);
-            p[i0] = make_float2(x0.x + t.x, x0.y + t.y);
-            p[i0 + h] = make_float2(x0.x - t.x, x0.y - t.y);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = buf[pad16(t + e * (N / 16))];
+}
+
+// One FFT pass along `axis` (0 = x, stride n^2; 1 = y, stride n; 2 = z,
+// stride 1) over T pencils per block, N/16 threads per pencil.  Radix-16
+// stages first, the remaining factor (2, 4 or 8) last; global memory is
+// read by the first stage and written by the last, in the same coalesced
+// pattern (z pass: along z; y and x passes: T consecutive z columns).
+template <int N, bool INV>
+__global__ void __launch_bounds__(kThreads)
+k_fft_pass(float2* __restrict__ data, int axis, int T, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int P = N / 16;                 // threads per pencil
+    int q, t;
+    if (axis == 2) { t = threadIdx.x % P; q = threadIdx.x / P; }
+    else { q = threadIdx.x % T; t = threadIdx.x / T; }
+    const long long nn = (long long)N * N;
+    long long base0, pstride, estride;
+    if (axis == 2) {
+        base0 = (long long)blockIdx.x * T * N;
+        pstride = N;
+        estride = 1;
+    } else {
+        const int per = N / T;
+        const long long outer = blockIdx.x / per;
+        const long long z0 = (long long)(blockIdx.x % per) * T;
+        base0 = (axis == 1 ? outer * nn : outer * N) + z0;
+        pstride = 1;
+        estride = axis == 1 ? N : nn;
+    }
+    const long long pb = base0 + q * pstride;
+    float2* buf = sm + q * pad16(N);
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = data[pb + (long long)(t + e * P) * estride];
+    fft_stage<N, 16, 1, INV>(v, t, tw);
+    if constexpr (N > 16) {
+        constexpr int R2 = N >= 256 ? 16 : N / 16;
+        exchange<N, 16, 1>(v, t, buf);
+        fft_stage<N, R2, 16, INV>(v, t, tw);
+        if constexpr (N > 256) {
+            constexpr int R3 = N / 256;
+            exchange<N, 16, 16>(v, t, buf);
+            fft_stage<N, R3, 256, INV>(v, t, tw);
         }
-        __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int q, j;
-        if (axis == 2) { q = idx / n; j = idx - q * n; }
-        else { j = idx / T; q = idx - j * T; }
-        data[base0 + q * pstride + j * estride] = buf[q * n + j];
-    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) data[pb + (long long)(t + e * P) * estride] = v[e];
 }
 
 // Shell of every mode (b = round(|m|); n/2 + 1 for modes outside 1..n/2)
@@ -198,56 +326,45 @@ __global__ void k_pm_mode_keys(int n, long long n3, unsigned long long* __restri
     vals[i] = (int)i;
 }
 
-// Per segment: sum of P and |k| over its modes (binary64, fixed order).
+// Per segment: sum over its modes of |delta_k|^2 / W^2 (terms in binary32,
+// the sum in binary64, fixed order).
 __global__ void __launch_bounds__(kThreads)
 k_pm_power_seg(const float2* __restrict__ dk, const int* __restrict__ perm, const int* __restrict__ seg_start,
-               const int* __restrict__ seg_len, const double* __restrict__ sinc4, int n, double pnorm,
-               double kfund, double* __restrict__ psum, double* __restrict__ ksum) {
-    __shared__ double sp[kThreads], sk[kThreads];
+               const int* __restrict__ seg_len, const float* __restrict__ inv_w2, int n,
+               double* __restrict__ psum) {
+    __shared__ double sp[kThreads];
     const int s = blockIdx.x;
     const int st = seg_start[s], len = seg_len[s];
-    const int h = n >> 1;
-    double ap = 0.0, ak = 0.0;
+    double ap = 0.0;
     for (int t = threadIdx.x; t < len; t += blockDim.x) {
-        const long long i = perm[st + t];
-        const int z = (int)(i % n), y = (int)((i / n) % n), x = (int)(i / ((long long)n * n));
+        const int i = perm[st + t];
+        const int z = i % n, y = (i / n) % n, x = i / (n * n);
         const float2 v = dk[i];
-        const double p2 = (double)v.x * v.x + (double)v.y * v.y;
-        ap += pnorm * p2 / (sinc4[x] * sinc4[y] * sinc4[z]);
-        const double mx = x < h ? x : x - n, my = y < h ? y : y - n, mz = z < h ? z : z - n;
-        ak += kfund * sqrt(mx * mx + my * my + mz * mz);
+        const float p2 = fmaf(v.x, v.x, v.y * v.y) * (inv_w2[x] * inv_w2[y] * inv_w2[z]);
+        ap += (double)p2;
     }
     sp[threadIdx.x] = ap;
-    sk[threadIdx.x] = ak;
     __syncthreads();
     for (int w = kThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sp[threadIdx.x] += sp[threadIdx.x + w];
-            sk[threadIdx.x] += sk[threadIdx.x + w];
-        }
+        if (threadIdx.x < w) sp[threadIdx.x] += sp[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        psum[s] = sp[0];
-        ksum[s] = sk[0];
-    }
+    if (threadIdx.x == 0) psum[s] = sp[0];
 }
 
-// Per shell: add its segments in order.
+// Per shell: add its segments in order; |k| means come from the table
+// made at creation (they do not depend on the particles).
 __global__ void k_pm_power_final(int nb, const int* __restrict__ bin_seg0, const int* __restrict__ bin_modes,
-                                 const double* __restrict__ psum, const double* __restrict__ ksum,
-                                 double* __restrict__ k_mean, double* __restrict__ power,
+                                 const double* __restrict__ psum, const double* __restrict__ kmean_tab,
+                                 double pnorm, double* __restrict__ k_mean, double* __restrict__ power,
                                  long long* __restrict__ modes) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
-    double p = 0.0, k = 0.0;
-    for (int s = bin_seg0[b]; s < bin_seg0[b + 1]; ++s) {
-        p += psum[s];
-        k += ksum[s];
-    }
+    double p = 0.0;
+    for (int s = bin_seg0[b]; s < bin_seg0[b + 1]; ++s) p += psum[s];
     const long long m = bin_modes[b];
-    if (k_mean) k_mean[b] = m ? k / (double)m : NAN;
-    if (power) power[b] = m ? p / (double)m : NAN;
+    if (k_mean) k_mean[b] = kmean_tab[b];
+    if (power) power[b] = m ? pnorm * p / (double)m : NAN;
     if (modes) modes[b] = m;
 }
 
@@ -304,33 +421,32 @@ k_cic_interp(const double* __restrict__ pos, long long np, double box, double in
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     int c[3];
-    double f[3];
+    float f[3];
     cic_cell(pos, i, box, inv_d, n, c, f);
-    double ax = 0.0, ay = 0.0, az = 0.0;
+    float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-        const double wx = dx ? f[0] : 1.0 - f[0];
-        const long long ix = (c[0] + dx) % n;
+        const float wx = dx ? f[0] : 1.f - f[0];
+        const long long ix = c[0] + dx == n ? 0 : c[0] + dx;
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
-            const double wy = dy ? f[1] : 1.0 - f[1];
-            const long long iy = (c[1] + dy) % n;
+            const float wxy = wx * (dy ? f[1] : 1.f - f[1]);
+            const long long iy = c[1] + dy == n ? 0 : c[1] + dy;
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
-                const double wz = dz ? f[2] : 1.0 - f[2];
-                const long long iz = (c[2] + dz) % n;
-                const double w = wx * wy * wz;
-                const float4 g = accg[(ix * n + iy) * n + iz];
-                ax += w * g.x;
-                ay += w * g.y;
-                az += w * g.z;
+                const float w = wxy * (dz ? f[2] : 1.f - f[2]);
+                const long long iz = c[2] + dz == n ? 0 : c[2] + dz;
+                const float4 g = __ldg(&accg[(ix * n + iy) * n + iz]);
+                ax = fmaf(w, g.x, ax);
+                ay = fmaf(w, g.y, ay);
+                az = fmaf(w, g.z, az);
             }
         }
     }
     float4 o = accumulate ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    o.x += (float)ax;
-    o.y += (float)ay;
-    o.z += (float)az;
+    o.x += ax;
+    o.y += ay;
+    o.z += az;
     acc[i] = o;
 }
 
@@ -348,16 +464,15 @@ struct sr_pm {
     float2* dk = nullptr;               // FFT of delta
     float2* work = nullptr;             // inverse-transform scratch
     float4* accg = nullptr;             // acceleration grid
-    float2* tw = nullptr;               // exp(-2 pi i k / n), k < n/2
-    double* sinc4 = nullptr;            // sinc^4(pi m / n) per axis index
-    float* inv_w2 = nullptr;            // 1 / sinc^4(pi m / n)
+    float2* tw = nullptr;               // exp(-2 pi i k / n), k < n
+    float* inv_w2 = nullptr;            // 1 / sinc^4(pi m / n) per axis index
+    double* kmean = nullptr;            // mean |k| per shell
     int* perm = nullptr;                // modes sorted by shell (shells 1..n/2 first)
     int* seg_start = nullptr;
     int* seg_len = nullptr;
     int* bin_seg0 = nullptr;            // first segment of each shell (n/2 + 1)
     int* bin_modes = nullptr;
     double* psum = nullptr;
-    double* ksum = nullptr;
     int n_seg = 0;
     long long last_np = 0;
     bool deposited = false;
@@ -374,23 +489,58 @@ int dalloc(T** p, long long count, const char* what) {
 }
 
 int pm_free(sr_pm* p) {
-    void* bufs[] = {p->fx, p->dk, p->work, p->accg, p->tw, p->sinc4, p->inv_w2, p->perm, p->seg_start,
-                    p->seg_len, p->bin_seg0, p->bin_modes, p->psum, p->ksum};
+    void* bufs[] = {p->fx, p->dk, p->work, p->accg, p->tw, p->inv_w2, p->kmean, p->perm, p->seg_start,
+                    p->seg_len, p->bin_seg0, p->bin_modes, p->psum};
     for (void* b : bufs) cudaFree(b);
     delete p;
     return SR_OK;
 }
 
-int fft3(sr_pm* p, float2* data, float sign, cudaStream_t st) {
-    const int n = p->n;
-    const int T = fft_pencils(n);
-    const size_t smem = fft_smem(n);
-    const unsigned blocks = (unsigned)((long long)n * n / T);
+template <int N, bool INV>
+int fft3_n(float2* data, const float2* tw, cudaStream_t st) {
+    const int T = fft_pencils(N);
+    const unsigned threads = (unsigned)(T * (N / 16));
+    const unsigned blocks = (unsigned)((long long)N * N / T);
     for (int axis = 2; axis >= 0; --axis) {
-        k_fft_pass<<<blocks, kThreads, smem, st>>>(data, n, p->logn, axis, T, p->tw, sign);
+        k_fft_pass<N, INV><<<blocks, threads, fft_smem(N), st>>>(data, axis, T, tw);
         SR_LAUNCH_CHECK("k_fft_pass");
     }
     return SR_OK;
+}
+
+template <bool INV>
+int fft3_dir(int n, float2* data, const float2* tw, cudaStream_t st) {
+    switch (n) {
+        case 16: return fft3_n<16, INV>(data, tw, st);
+        case 32: return fft3_n<32, INV>(data, tw, st);
+        case 64: return fft3_n<64, INV>(data, tw, st);
+        case 128: return fft3_n<128, INV>(data, tw, st);
+        case 256: return fft3_n<256, INV>(data, tw, st);
+        case 512: return fft3_n<512, INV>(data, tw, st);
+        case 1024: return fft3_n<1024, INV>(data, tw, st);
+        default: return sr::set_error(SR_ERR_ARG, "fft: unsupported size");
+    }
+}
+
+int fft3(sr_pm* p, float2* data, float sign, cudaStream_t st) {
+    return sign < 0.f ? fft3_dir<false>(p->n, data, p->tw, st) : fft3_dir<true>(p->n, data, p->tw, st);
+}
+
+template <int N, bool INV>
+cudaError_t fft_attr() {
+    return cudaFuncSetAttribute(k_fft_pass<N, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(N));
+}
+
+cudaError_t fft_attrs(int n) {
+    switch (n) {
+        case 16: { cudaError_t e = fft_attr<16, false>(); return e ? e : fft_attr<16, true>(); }
+        case 32: { cudaError_t e = fft_attr<32, false>(); return e ? e : fft_attr<32, true>(); }
+        case 64: { cudaError_t e = fft_attr<64, false>(); return e ? e : fft_attr<64, true>(); }
+        case 128: { cudaError_t e = fft_attr<128, false>(); return e ? e : fft_attr<128, true>(); }
+        case 256: { cudaError_t e = fft_attr<256, false>(); return e ? e : fft_attr<256, true>(); }
+        case 512: { cudaError_t e = fft_attr<512, false>(); return e ? e : fft_attr<512, true>(); }
+        default: { cudaError_t e = fft_attr<1024, false>(); return e ? e : fft_attr<1024, true>(); }
+    }
 }
 
 // Mode permutation by shell and the segment tables (once, synchronous).
@@ -414,10 +564,12 @@ int build_shells(sr_pm* p) {
     int kb = 1;
     while ((1 << kb) <= p->n / 2 + 1) ++kb;
     if (!rc) rc = sr::radix_sort_pairs(keys, vals, (int)n3, kb, rs, nullptr, &which);
-    // modes per shell, counted on the host with the same classification
+    // modes and mean |k| per shell, on the host with the same classification
     std::vector<int> modes(p->n / 2 + 2, 0);
+    std::vector<double> ksum(p->n / 2 + 2, 0.0);
     if (!rc) {
         const int n = p->n, h = n / 2;
+        const double kf = 2.0 * 3.14159265358979323846 / p->box;
         std::vector<long long> sq(n);
         for (int i = 0; i < n; ++i) {
             const long long m = i < h ? i : i - n;
@@ -426,8 +578,11 @@ int build_shells(sr_pm* p) {
         for (int x = 0; x < n; ++x)
             for (int y = 0; y < n; ++y)
                 for (int z = 0; z < n; ++z) {
-                    const int b = (int)std::rint(std::sqrt((double)(sq[x] + sq[y] + sq[z])));
-                    modes[(b >= 1 && b <= h) ? b : h + 1]++;
+                    const double r = std::sqrt((double)(sq[x] + sq[y] + sq[z]));
+                    const int b = (int)std::rint(r);
+                    const int sh = (b >= 1 && b <= h) ? b : h + 1;
+                    modes[sh]++;
+                    ksum[sh] += kf * r;
                 }
     }
     if (!rc) {
@@ -445,13 +600,15 @@ int build_shells(sr_pm* p) {
         bin_seg0[nb] = (int)seg_start.size();
         p->n_seg = (int)seg_start.size();
         std::vector<int> bm(modes.begin() + 1, modes.begin() + 1 + nb);
+        std::vector<double> km(nb);
+        for (int b = 1; b <= nb; ++b) km[b - 1] = ksum[b] / modes[b];
         rc = dalloc(&p->perm, n3, "sr_pm_create perm");
         if (!rc) rc = dalloc(&p->seg_start, p->n_seg, "seg_start");
         if (!rc) rc = dalloc(&p->seg_len, p->n_seg, "seg_len");
         if (!rc) rc = dalloc(&p->bin_seg0, nb + 1, "bin_seg0");
         if (!rc) rc = dalloc(&p->bin_modes, nb, "bin_modes");
         if (!rc) rc = dalloc(&p->psum, p->n_seg, "psum");
-        if (!rc) rc = dalloc(&p->ksum, p->n_seg, "ksum");
+        if (!rc) rc = dalloc(&p->kmean, nb, "kmean");
         cudaError_t e = cudaSuccess;
         if (!rc) e = cudaMemcpy(p->perm, vals[which], sizeof(int) * n3, cudaMemcpyDeviceToDevice);
         if (!rc && e == cudaSuccess)
@@ -461,6 +618,7 @@ int build_shells(sr_pm* p) {
         if (!rc && e == cudaSuccess)
             e = cudaMemcpy(p->bin_seg0, bin_seg0.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice);
         if (!rc && e == cudaSuccess) e = cudaMemcpy(p->bin_modes, bm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+        if (!rc && e == cudaSuccess) e = cudaMemcpy(p->kmean, km.data(), sizeof(double) * nb, cudaMemcpyHostToDevice);
         if (!rc && e != cudaSuccess) rc = sr::cuda_fail(e, "sr_pm_create tables");
     }
     for (int k = 0; k < 2; ++k) {
@@ -480,8 +638,8 @@ int sr_pm_create(int n_grid, double box, double sigma, int64_t n_max, sr_pm** ou
     *out = nullptr;
     int logn = 0;
     while ((1 << logn) < n_grid) ++logn;
-    if (n_grid < 8 || n_grid > 1024 || (1 << logn) != n_grid)
-        return sr::set_error(SR_ERR_ARG, "sr_pm_create: n_grid must be a power of two in [8, 1024]");
+    if (n_grid < 16 || n_grid > 1024 || (1 << logn) != n_grid)
+        return sr::set_error(SR_ERR_ARG, "sr_pm_create: n_grid must be a power of two in [16, 1024]");
     if (!(box > 0.0) || !std::isfinite(box) || !(sigma >= 0.0) || !std::isfinite(sigma))
         return sr::set_error(SR_ERR_ARG, "sr_pm_create: box must be > 0 and sigma >= 0");
     if (n_max < 1 || n_max > 2147483647LL) return sr::set_error(SR_ERR_ARG, "sr_pm_create: bad n_max");
@@ -501,33 +659,28 @@ int sr_pm_create(int n_grid, double box, double sigma, int64_t n_max, sr_pm** ou
     if (!rc) rc = dalloc(&p->dk, p->n3, "sr_pm_create dk");
     if (!rc) rc = dalloc(&p->work, p->n3, "sr_pm_create work");
     if (!rc) rc = dalloc(&p->accg, p->n3, "sr_pm_create accel grid");
-    if (!rc) rc = dalloc(&p->tw, n_grid / 2, "sr_pm_create twiddles");
-    if (!rc) rc = dalloc(&p->sinc4, n_grid, "sr_pm_create sinc");
+    if (!rc) rc = dalloc(&p->tw, n_grid, "sr_pm_create twiddles");
     if (!rc) rc = dalloc(&p->inv_w2, n_grid, "sr_pm_create window");
     if (!rc) {
-        std::vector<float2> tw(n_grid / 2);
+        std::vector<float2> tw(n_grid);
         const double pi = 3.14159265358979323846;
-        for (int k = 0; k < n_grid / 2; ++k) {
+        for (int k = 0; k < n_grid; ++k) {
             const double a = -2.0 * pi * k / n_grid;
             tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
-        std::vector<double> s4(n_grid);
         std::vector<float> iw(n_grid);
         for (int i = 0; i < n_grid; ++i) {
             const int m = i < n_grid / 2 ? i : i - n_grid;
             const double hh = pi * m / n_grid;
             const double s = m == 0 ? 1.0 : std::sin(hh) / hh;
-            s4[i] = s * s * s * s;
-            iw[i] = (float)(1.0 / s4[i]);
+            iw[i] = (float)(1.0 / (s * s * s * s));
         }
         cudaError_t e = cudaMemcpy(p->tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(p->sinc4, s4.data(), sizeof(double) * n_grid, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->inv_w2, iw.data(), sizeof(float) * n_grid, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = sr::cuda_fail(e, "sr_pm_create tables");
     }
     if (!rc) {
-        const size_t smem = fft_smem(n_grid);
-        cudaError_t e = cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = fft_attrs(n_grid);
         if (e != cudaSuccess) rc = sr::cuda_fail(e, "sr_pm_create fft smem");
     }
     if (!rc) rc = build_shells(p);
@@ -552,7 +705,7 @@ int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream) {
     const double scale = std::ldexp(1.0, pm->fixed_shift);
     SR_CUDA_CHECK(cudaMemsetAsync(pm->fx, 0, sizeof(unsigned long long) * (size_t)pm->n3, st));
     k_cic_deposit<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box, pm->n,
-                                                              scale, pm->fx);
+                                                              (float)scale, pm->fx);
     SR_LAUNCH_CHECK("k_cic_deposit");
     const double inv_nbar = (double)pm->n3 / (double)n;
     k_pm_delta<<<grid_for(pm->n3, kThreads), kThreads, 0, st>>>(pm->fx, pm->n3, 1.0 / scale, inv_nbar, pm->dk);
@@ -571,13 +724,12 @@ int sr_pm_power(sr_pm* pm, double* k_mean, double* power, int64_t* modes, void* 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double n6 = (double)pm->n3 * (double)pm->n3;
     const double pnorm = pm->box * pm->box * pm->box / n6;
-    const double kf = 2.0 * 3.14159265358979323846 / pm->box;
-    k_pm_power_seg<<<pm->n_seg, kThreads, 0, st>>>(pm->dk, pm->perm, pm->seg_start, pm->seg_len, pm->sinc4, pm->n,
-                                                   pnorm, kf, pm->psum, pm->ksum);
+    k_pm_power_seg<<<pm->n_seg, kThreads, 0, st>>>(pm->dk, pm->perm, pm->seg_start, pm->seg_len, pm->inv_w2, pm->n,
+                                                   pm->psum);
     SR_LAUNCH_CHECK("k_pm_power_seg");
     const int nb = pm->n / 2;
-    k_pm_power_final<<<grid_for(nb, 128), 128, 0, st>>>(nb, pm->bin_seg0, pm->bin_modes, pm->psum, pm->ksum, k_mean,
-                                                        power, reinterpret_cast<long long*>(modes));
+    k_pm_power_final<<<grid_for(nb, 128), 128, 0, st>>>(nb, pm->bin_seg0, pm->bin_modes, pm->psum, pm->kmean, pnorm,
+                                                        k_mean, power, reinterpret_cast<long long*>(modes));
     SR_LAUNCH_CHECK("k_pm_power_final");
     return SR_OK;
 }

@@ -105,7 +105,7 @@ def test_pm_argument_checks_need_no_device(lib):
     create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(v)]
     h = v()
     assert create(100, 10.0, 0.8, 10, ctypes.byref(h)) == 1 and not h.value    # not a power of two
-    assert create(4, 10.0, 0.8, 10, ctypes.byref(h)) == 1                      # too small
+    assert create(8, 10.0, 0.8, 10, ctypes.byref(h)) == 1                      # too small
     assert create(2048, 10.0, 0.8, 10, ctypes.byref(h)) == 1                   # too large
     assert create(64, -1.0, 0.8, 10, ctypes.byref(h)) == 1
     assert create(64, 10.0, -0.5, 10, ctypes.byref(h)) == 1

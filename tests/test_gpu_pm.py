@@ -27,7 +27,7 @@ def _pm(ng, box, sigma, n):
     return PM(ng, box, sigma, n)
 
 
-@pytest.mark.parametrize("ng", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("ng", [16, 32, 64, 128, 256, 512])
 def test_fft_matches_library_fft(ng):
     rng = np.random.default_rng(ng)
     x = (rng.standard_normal((ng, ng, ng)) + 1j * rng.standard_normal((ng, ng, ng))).astype(np.complex64)
@@ -59,8 +59,9 @@ def test_deposit_delta_k_and_power(clustered, ng):
     p.deposit(x)
     counts = p.export("counts").cpu().numpy()
     ref = opm.cic_deposit(pos, box, ng)
-    assert np.max(np.abs(counts - ref)) <= 1e-9 * max(1.0, ref.max())
-    assert counts.sum() == pytest.approx(len(pos), rel=1e-12)
+    # corner weights are binary32 (relative error a few 2^-24 each)
+    assert np.all(np.abs(counts - ref) <= 4e-7 * np.maximum(ref, 1.0))
+    assert counts.sum() == pytest.approx(len(pos), rel=1e-6)
     dk = p.export("delta_k").cpu().numpy()
     dref = np.fft.fftn(ref / (len(pos) / ng ** 3) - 1.0)
     assert np.linalg.norm(dk - dref) <= FFT_TOL * np.linalg.norm(dref)
