@@ -48,8 +48,10 @@ inline int fft_pencils(int n) {
     return t > n ? n : t;
 }
 
+__host__ __device__ constexpr int pencil_stride(int n);
+
 inline size_t fft_smem(int n) {
-    return sizeof(float2) * (size_t)fft_pencils(n) * (size_t)(n + n / 16);
+    return sizeof(float2) * (size_t)fft_pencils(n) * (size_t)pencil_stride(n);
 }
 
 // x mod L in [0, L) (fmod, then + L for a negative remainder, a result of
@@ -247,6 +249,11 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[16], int t, const float2* 
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
+// Shared-memory stride between a block's pencils: one slot per 16 points
+// plus one, an odd number of 8-byte slots, so that the 16 pencils a half
+// warp touches in the y and x passes fall in different banks.
+__host__ __device__ constexpr int pencil_stride(int n) { return n + n / 16 + 1; }
+
 // Outputs of stage (R, S) to shared memory, then element t + e N/16 back
 // into register e.
 template <int N, int R, int S>
@@ -293,7 +300,7 @@ k_fft_pass(float2* __restrict__ data, int axis, int T, const float2* __restrict_
         estride = axis == 1 ? N : nn;
     }
     const long long pb = base0 + q * pstride;
-    float2* buf = sm + q * pad16(N);
+    float2* buf = sm + q * pencil_stride(N);
     float2 v[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = data[pb + (long long)(t + e * P) * estride];
