@@ -46,7 +46,7 @@ typedef struct sr_pm sr_pm;
 
 /* Export selectors for sr_pm_copy (device destination). */
 #define SR_PM_EXPORT_COUNTS   0  /* binary64[n_g^3]: CIC counts of the last deposit            */
-#define SR_PM_EXPORT_DELTA_K  1  /* float2[n_g^3]: FFT of delta of the last deposit              */
+#define SR_PM_EXPORT_DELTA_K  1  /* float2[n_g^3]: FFT of delta of the last transform            */
 #define SR_PM_EXPORT_ACCEL    2  /* float4[n_g^3]: long-range acceleration on the grid (x,y,z,0) */
 
 /*
@@ -63,25 +63,32 @@ int sr_pm_destroy(sr_pm* pm);
 
 /*
  * sr_pm_deposit -- CIC counts of n particles (pos: device, n rows (x,y,z)
- * binary64, any finite values, folded into [0, L)), delta and its forward
- * FFT.  Errors: SR_ERR_ARG (null, n < 1), SR_ERR_CAPACITY (n > n_max).
+ * binary64, any finite values, folded into [0, L)).
+ * Errors: SR_ERR_ARG (null, n < 1), SR_ERR_CAPACITY (n > n_max).
  */
 int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream);
 
 /*
- * sr_pm_power -- the power spectrum of the last deposit: k_mean, power
+ * sr_pm_transform -- delta of the last deposit and its forward FFT, the
+ * input of sr_pm_power and sr_pm_force.  Errors: SR_ERR_STATE before a
+ * deposit.
+ */
+int sr_pm_transform(sr_pm* pm, void* stream);
+
+/*
+ * sr_pm_power -- the power spectrum of the last transform: k_mean, power
  * (binary64) and modes (int64) per shell b = 1 .. n_g/2, device arrays of
  * n_g/2 entries each (nullable individually).  Errors: SR_ERR_STATE before a
- * deposit.
+ * transform.
  */
 int sr_pm_power(sr_pm* pm, double* k_mean, double* power, int64_t* modes, void* stream);
 
 /*
- * sr_pm_force -- long-range accelerations of the last deposit's density,
+ * sr_pm_force -- long-range accelerations of the last transform's density,
  * interpolated at the n particles pos (usually the deposited ones) into
  * acc (device, float4 rows (x, y, z, w)); accumulate = 0 overwrites x, y, z
  * and sets w = 0, accumulate = 1 adds to x, y, z (e.g. onto the short-range
- * accelerations of sr_force).  Errors: SR_ERR_STATE before a deposit,
+ * accelerations of sr_force).  Errors: SR_ERR_STATE before a transform,
  * SR_ERR_ARG, SR_ERR_CAPACITY.
  */
 int sr_pm_force(sr_pm* pm, const double* pos, int64_t n, float* acc, int accumulate, void* stream);

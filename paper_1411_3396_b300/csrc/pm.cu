@@ -483,6 +483,7 @@ struct sr_pm {
     int n_seg = 0;
     long long last_np = 0;
     bool deposited = false;
+    bool transformed = false;
     bool accel_valid = false;
 };
 
@@ -714,20 +715,31 @@ int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream) {
     k_cic_deposit<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box, pm->n,
                                                               (float)scale, pm->fx);
     SR_LAUNCH_CHECK("k_cic_deposit");
-    const double inv_nbar = (double)pm->n3 / (double)n;
-    k_pm_delta<<<grid_for(pm->n3, kThreads), kThreads, 0, st>>>(pm->fx, pm->n3, 1.0 / scale, inv_nbar, pm->dk);
+    pm->last_np = n;
+    pm->deposited = true;
+    pm->transformed = false;
+    pm->accel_valid = false;
+    return SR_OK;
+}
+
+int sr_pm_transform(sr_pm* pm, void* stream) {
+    if (!pm) return sr::set_error(SR_ERR_ARG, "sr_pm_transform: null workspace");
+    if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_transform: call sr_pm_deposit first");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double inv_nbar = (double)pm->n3 / (double)pm->last_np;
+    k_pm_delta<<<grid_for(pm->n3, kThreads), kThreads, 0, st>>>(pm->fx, pm->n3, std::ldexp(1.0, -pm->fixed_shift),
+                                                                inv_nbar, pm->dk);
     SR_LAUNCH_CHECK("k_pm_delta");
     int rc = fft3(pm, pm->dk, -1.f, st);
     if (rc) return rc;
-    pm->last_np = n;
-    pm->deposited = true;
+    pm->transformed = true;
     pm->accel_valid = false;
     return SR_OK;
 }
 
 int sr_pm_power(sr_pm* pm, double* k_mean, double* power, int64_t* modes, void* stream) {
     if (!pm) return sr::set_error(SR_ERR_ARG, "sr_pm_power: null workspace");
-    if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_power: call sr_pm_deposit first");
+    if (!pm->transformed) return sr::set_error(SR_ERR_STATE, "sr_pm_power: call sr_pm_transform first");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double n6 = (double)pm->n3 * (double)pm->n3;
     const double pnorm = pm->box * pm->box * pm->box / n6;
@@ -743,7 +755,7 @@ int sr_pm_power(sr_pm* pm, double* k_mean, double* power, int64_t* modes, void* 
 
 int sr_pm_force(sr_pm* pm, const double* pos, int64_t n, float* acc, int accumulate, void* stream) {
     if (!pm || !pos || !acc) return sr::set_error(SR_ERR_ARG, "sr_pm_force: null argument");
-    if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_force: call sr_pm_deposit first");
+    if (!pm->transformed) return sr::set_error(SR_ERR_STATE, "sr_pm_force: call sr_pm_transform first");
     if (n < 1) return sr::set_error(SR_ERR_ARG, "sr_pm_force: n must be >= 1");
     if (n > pm->n_max) return sr::set_error(SR_ERR_CAPACITY, "sr_pm_force: n above n_max");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -784,7 +796,8 @@ int sr_pm_copy(sr_pm* pm, int what, void* dst, void* stream) {
     if (!pm || !dst) return sr::set_error(SR_ERR_ARG, "sr_pm_copy: null argument");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (what == SR_PM_EXPORT_COUNTS || what == SR_PM_EXPORT_DELTA_K) {
-        if (!pm->deposited) return sr::set_error(SR_ERR_STATE, "sr_pm_copy: nothing deposited");
+        if (!pm->deposited || (what == SR_PM_EXPORT_DELTA_K && !pm->transformed))
+            return sr::set_error(SR_ERR_STATE, "sr_pm_copy: nothing deposited or transformed");
         if (what == SR_PM_EXPORT_COUNTS) {
             k_pm_counts<<<grid_for(pm->n3, kThreads), kThreads, 0, st>>>(pm->fx, pm->n3,
                                                                          std::ldexp(1.0, -pm->fixed_shift),

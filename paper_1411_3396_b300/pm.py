@@ -42,9 +42,16 @@ class PM:
         except Exception:
             pass
 
-    def deposit(self, pos: torch.Tensor):
+    def deposit(self, pos: torch.Tensor, transform: bool = True):
+        """CIC counts of pos; with transform, also delta and its FFT (the
+        input of power() and force())."""
         _check_pos(pos)
         check(load().sr_pm_deposit(self._h, _ptr(pos), int(pos.shape[0]), _stream()))
+        if transform:
+            self.transform()
+
+    def transform(self):
+        check(load().sr_pm_transform(self._h, _stream()))
 
     def power(self):
         """(k_mean, P, modes) per shell b = 1 .. n_grid/2 (device tensors)."""

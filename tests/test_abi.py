@@ -110,7 +110,8 @@ def test_pm_argument_checks_need_no_device(lib):
     assert create(64, -1.0, 0.8, 10, ctypes.byref(h)) == 1
     assert create(64, 10.0, -0.5, 10, ctypes.byref(h)) == 1
     assert create(64, 10.0, 0.8, 0, ctypes.byref(h)) == 1
-    for name, nargs in (("sr_pm_deposit", 4), ("sr_pm_power", 5), ("sr_pm_fft", 4), ("sr_pm_copy", 4)):
+    for name, nargs in (("sr_pm_deposit", 4), ("sr_pm_transform", 2), ("sr_pm_power", 5), ("sr_pm_fft", 4),
+                        ("sr_pm_copy", 4)):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         assert f(*([None] * nargs)) == 1, name

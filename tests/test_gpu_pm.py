@@ -123,6 +123,9 @@ def test_pm_state_and_argument_errors():
     x = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(SrError):
         p.power()                                         # nothing deposited yet
+    p.deposit(x, transform=False)
+    with pytest.raises(SrError):
+        p.force(x)                                        # deposited, not transformed
     with pytest.raises(SrError):
         p.force(x)
     big = torch.zeros((101, 3), dtype=torch.float64, device="cuda")
