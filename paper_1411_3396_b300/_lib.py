@@ -1,5 +1,5 @@
-"""ctypes declarations of the C ABI in include/sr.h, include/sr_centers.h and
-include/sr_pm.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/sr.h, include/sr_centers.h,
+include/sr_pm.h and include/sr_fof.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -34,6 +34,11 @@ class SrCentersInfo(ctypes.Structure):
                 ("max_members", c_int64), ("pairs", c_int64), ("items", c_int64),
                 ("evaluated", c_int64), ("fixed_shift", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("bad_labels", c_int64), ("wide_members", c_int64)]
+
+
+class SrFofInfo(ctypes.Structure):
+    _fields_ = [("n_particles", c_int64), ("n_halos", c_int64), ("n_members", c_int64),
+                ("max_members", c_int64), ("links", c_int64), ("band_checks", c_int64), ("error", c_int64)]
 
 
 class SrError(RuntimeError):
@@ -85,6 +90,10 @@ SIGNATURES = {
     "sr_pm_force": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]),
     "sr_pm_fft": (c_int, [c_void_p, c_void_p, c_int, c_void_p]),
     "sr_pm_copy": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "sr_fof_create": (c_int, [c_int64, POINTER(c_void_p)]),
+    "sr_fof_destroy": (c_int, [c_void_p]),
+    "sr_fof_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, c_int, c_void_p, c_void_p, c_void_p]),
+    "sr_fof_get_info": (c_int, [c_void_p, POINTER(SrFofInfo)]),
     "sr_last_error": (c_char_p, []),
     "sr_launch_count": (c_int64, []),
 }

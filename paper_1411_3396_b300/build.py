@@ -17,7 +17,7 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libsr_b300.so"
 SOURCES = ["abi.cu", "fit.cpp", "radix.cu", "bin.cu", "force.cu", "plain.cu", "kick.cu", "noalloc.cu",
-           "centers.cu", "pm.cu"]
+           "centers.cu", "pm.cu", "fof.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
