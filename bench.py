@@ -423,6 +423,7 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
 
 
+FOF_FLOPS_PER_TEST = 11    # 3 adds (anchor shift), 3 differences, 1 mul + 2 FMA for |d|^2
 MUFU_PER_SM_CLK = 16      # rsqrt results per SM per clock (measured on B300: 16; ex2 runs at 32)
 
 
@@ -764,6 +765,154 @@ def run_pm(args, rank, world, local_rank):
     pm.close()
 
 
+def cpu_fof_sample(seed_n=128 ** 3, link=0.168):
+    """Time the FP64 oracle's FOF (k-d tree pairs, exact predicate, graph
+    components) on the clustered set resized to seed_n particles."""
+    from oracle import fof as ofof
+    pos, box, _ = _pm_inputs(seed_n)
+    t0 = time.perf_counter()
+    ofof.fof(pos, box, link, 40)
+    secs = time.perf_counter() - t0
+    return len(pos) / secs, len(pos), secs
+
+
+def run_fof(args, rank, world, local_rank):
+    """Friends-of-friends on the clustered 256^3 set (linking length 0.168
+    mean spacings, halos of at least 40 particles), then the most-bound
+    particle of every FOF halo: the in-situ analysis chain.  One step =
+    sr_bin + sr_fof_run (+ the center finder, timed separately).  Metric:
+    particles per second through binning and FOF."""
+    pos, box, _ = _pm_inputs(args.n_particles)
+    n = len(pos)
+    link = args.fof_b * box / round(n ** (1.0 / 3.0))
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        rate, cn, secs = cpu_fof_sample(link=args.fof_b)
+        cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": f"the same clustered catalogue resized to {cn} particles, FOF in {secs:.1f} s "
+                         "(FP64 k-d tree pairs + exact predicate + graph components)"}
+
+    import torch
+
+    from paper_1411_3396_b300 import FOF, Centers, Plan, launch_count
+    from workloads import configs as wc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    prm = wc.CONFIGS["clustered256"]
+    x = torch.from_numpy(pos).to(dev)
+    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n)
+    fof = FOF(n)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    hsizes = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        plan.bin(x)
+        if ev is not None:
+            ev[1].record()
+        fof.run(plan, x, link, 40, labels, hsizes)
+        if ev is not None:
+            ev[2].record()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = fof.info()
+    uuid = str(getattr(props, "uuid", "")) if hasattr(props, "uuid") else ""
+    sampler = ClockSampler(uuid if rank == 0 else "")
+    if rank == 0 and not args.no_clocks:
+        sampler.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    t_start.record()
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    l1 = launch_count()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
+    ms = t_start.elapsed_time(t_end) / args.steps
+    bin_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    fof_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    n_all, ms_max = reduce_over_ranks(n, ms, world, dev)
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = info["tests"] * FOF_FLOPS_PER_TEST / (fof_ms * 1e-3) / 1e12
+
+    # end to end: positions from pinned host memory, labels back
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(pos).pin_memory()
+        lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        ts = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x.copy_(pos_h, non_blocking=True)
+            step()
+            lab_h.copy_(labels, non_blocking=True)
+            torch.cuda.synchronize()
+            if k:
+                ts.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(ts))
+        e2e = {"value": n / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": int(n * 24),
+               "d2h_bytes_per_step": int(n * 4), "ms_per_step": e2e_s * 1e3}
+
+    # centers of the FOF halos (the catalogue the paper's center finder reads)
+    nh = int(info["n_halos"])
+    ctr = Centers(n, max(nh, 1))
+    phi, cen, cphi = ctr.run(x, labels, nh, box, prm["eps"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctr.run(x, labels, nh, box, prm["eps"], phi, cen, cphi)
+    e1.record()
+    torch.cuda.synchronize()
+    cinfo = ctr.info()
+    centers_ms = e0.elapsed_time(e1)
+    ctr.close()
+    fof.close()
+    plan.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "friends-of-friends halo finding (b=0.168, >=40 particles) incl. binning: particles/sec",
+        "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "fof256", "catalogue": "clustered256 particles", "n_particles": n, "box": box,
+                   "link": link, "b": args.fof_b, "min_members": 40, "bin_ms": bin_ms, "fof_ms": fof_ms,
+                   "n_halos": nh, "n_members": info["n_members"], "max_members": info["max_members"],
+                   "links": info["links"], "band_checks": info["band_checks"],
+                   "centers_of_fof_halos": {"ms": centers_ms, "pairs": cinfo["pairs"],
+                                            "pairs_per_s": cinfo["pairs"] / (centers_ms * 1e-3)},
+                   "l2": "inputs larger than L2 (402 MB positions); no flush",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_fof_pairs",
+                     "kernel_ms": fof_ms, "flops_per_test": FOF_FLOPS_PER_TEST, "tests": info["tests"],
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   "(derived); the kernel is bound by union-find and load latency, not by the ALU"},
+        "e2e": e2e,
+        "gpu_launches": int(l1 - l0),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_centers(args, rank, world):
     pos, box, lab, nh, eps = _centers_inputs(args.n_particles)
     if rank != 0:
@@ -935,6 +1084,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--n-grid", type=int, default=0, help="PM mesh points per axis (0 = cube root of n)")
+    ap.add_argument("--fof-b", type=float, default=0.168, help="FOF linking length in mean spacings")
     ap.add_argument("--cpu-center-terms", type=int, default=250_000_000,
                     help="ordered member pairs in the oracle's center-finder sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -969,6 +1119,8 @@ def main():
         run_centers(args, rank, world, local_rank)
     elif args.workload == "pm256":
         run_pm(args, rank, world, local_rank)
+    elif args.workload == "fof256":
+        run_fof(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -45,6 +45,7 @@ typedef struct sr_fof_info {
     int64_t max_members;   /* largest halo                                        */
     int64_t links;         /* friend pairs found (each unordered pair once)       */
     int64_t band_checks;   /* pairs decided by the binary64 test                  */
+    int64_t tests;         /* particle pairs tested with the binary32 predicate   */
     int64_t error;         /* 0, or 1 if a union-find loop hit its iteration bound */
 } sr_fof_info;
 

@@ -38,7 +38,8 @@ class SrCentersInfo(ctypes.Structure):
 
 class SrFofInfo(ctypes.Structure):
     _fields_ = [("n_particles", c_int64), ("n_halos", c_int64), ("n_members", c_int64),
-                ("max_members", c_int64), ("links", c_int64), ("band_checks", c_int64), ("error", c_int64)]
+                ("max_members", c_int64), ("links", c_int64), ("band_checks", c_int64), ("tests", c_int64),
+                ("error", c_int64)]
 
 
 class SrError(RuntimeError):

@@ -35,7 +35,8 @@ struct FofCtr {
     unsigned long long err;
     unsigned long long members;
     unsigned long long max_members;
-    unsigned long long reserved[2];
+    unsigned long long tests;
+    unsigned long long reserved;
 };
 
 __device__ __forceinline__ double fold(double v, double box) {
@@ -110,7 +111,7 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
     constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
     const int n_items = ccs[total_cells];
-    unsigned long long my_links = 0, my_band = 0;
+    unsigned long long my_links = 0, my_band = 0, my_tests = 0;
     while (true) {
         int item = 0;
         if (lane == 0) item = (int)atomicAdd(&c->queue, 1ull);
@@ -128,11 +129,14 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
         const int q[3] = {m.x, m.y, m.z};
         const float ilo[3] = {lo.x, lo.y, lo.z}, ihi[3] = {hi.x, hi.y, hi.z};
         float4 pi[K];
-        int ii[K];
+        int ii[K], ri[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             pi[k] = slot_pos[(long long)I * C + lane + 32 * k];
             ii[k] = slot_idx[(long long)I * C + lane + 32 * k];
+            // an ancestor of the particle's group root: a friend whose root
+            // equals it is already joined
+            ri[k] = ii[k] >= 0 ? find_root(parent, ii[k], c) : -1;
         }
         const int b = V.sub_bits;
         int cc[3], olo[3], ohi[3];
@@ -197,6 +201,7 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
                                     for (int k = 0; k < K; ++k) {
                                         const int is = lane + 32 * k;
                                         if (ii[k] < 0 || jidx < 0 || (Jl == I && js <= is)) continue;
+                                        ++my_tests;
                                         const float dx = xj - pi[k].x, dy = yj - pi[k].y, dz = zj - pi[k].z;
                                         const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                                         if (s < hi_thr) {
@@ -207,7 +212,10 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
                                             }
                                             if (f) {
                                                 ++my_links;
-                                                unite(parent, ii[k], jidx, c);
+                                                if (find_root(parent, jidx, c) != ri[k]) {
+                                                    unite(parent, ii[k], jidx, c);
+                                                    ri[k] = find_root(parent, ii[k], c);
+                                                }
                                             }
                                         }
                                     }
@@ -223,10 +231,12 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
     for (int o = 16; o > 0; o >>= 1) {
         my_links += __shfl_xor_sync(kFull, my_links, o);
         my_band += __shfl_xor_sync(kFull, my_band, o);
+        my_tests += __shfl_xor_sync(kFull, my_tests, o);
     }
     if (lane == 0) {
         if (my_links) atomicAdd(&c->links, my_links);
         if (my_band) atomicAdd(&c->band, my_band);
+        if (my_tests) atomicAdd(&c->tests, my_tests);
     }
 }
 
@@ -393,6 +403,7 @@ int sr_fof_get_info(sr_fof* f, sr_fof_info* out) {
     out->max_members = (int64_t)h.max_members;
     out->links = (int64_t)h.links;
     out->band_checks = (int64_t)h.band;
+    out->tests = (int64_t)h.tests;
     out->error = h.err ? 1 : 0;
     return SR_OK;
 }

@@ -119,3 +119,21 @@ def test_pm_argument_checks_need_no_device(lib):
     assert lib.sr_pm_force(None, None, ctypes.c_int64(0), None, 0, None) == 1
     lib.sr_pm_destroy.restype = ctypes.c_int
     assert lib.sr_pm_destroy(None) == 0
+
+
+def test_fof_argument_checks_need_no_device(lib):
+    v = ctypes.c_void_p
+    create = lib.sr_fof_create
+    create.restype = ctypes.c_int
+    create.argtypes = [ctypes.c_int64, ctypes.POINTER(v)]
+    h = v()
+    assert create(0, ctypes.byref(h)) == 1 and not h.value
+    assert create(1 << 31, ctypes.byref(h)) == 1
+    run = lib.sr_fof_run
+    run.restype = ctypes.c_int
+    run.argtypes = [v, v, v, ctypes.c_int64, ctypes.c_double, ctypes.c_int, v, v, v]
+    assert run(None, None, None, 0, 0.2, 40, None, None, None) == 1
+    lib.sr_fof_get_info.restype = ctypes.c_int
+    assert lib.sr_fof_get_info(None, None) == 1
+    lib.sr_fof_destroy.restype = ctypes.c_int
+    assert lib.sr_fof_destroy(None) == 0
