@@ -80,9 +80,10 @@ def test_pair_counts_bit_exact(small_case):
 
 
 def test_all_kernel_variants_give_identical_forces(small_case):
-    # variants 0-6 share the summation order of the counting kernel; 7-11
-    # (scalar split sums and the packed two-wide loop) add even and odd
-    # neighbours separately and agree with each other bit for bit
+    # variants 0-6 share the summation order of the counting kernel; the
+    # packed two-wide variants 8-11 share theirs (batches of 64 neighbours,
+    # even and odd entries apart) and agree bit for bit; 7 (scalar split
+    # sums, batches of 32) and all of them agree with the oracle
     from paper_1411_3396_b300 import SrError
     name, w, chunk = small_case
     plan, acc_c, _, _ = _gpu(w["volumes"], w["params"], count=True, chunk_size=chunk)
@@ -96,15 +97,17 @@ def test_all_kernel_variants_give_identical_forces(small_case):
         with pytest.raises(SrError):
             plan.set_variant(8)
         return
-    split = None
     a_ref, _ = oracle_force(w["volumes"], w["params"])
-    for v in range(7, 12):
+    plan.set_variant(7)
+    assert_force_close(to_np(plan.force()), a_ref, f"{name} variant 7")
+    packed = None
+    for v in range(8, 12):
         plan.set_variant(v)
         acc = to_np(plan.force())
-        if split is None:
-            split = acc
+        if packed is None:
+            packed = acc
             assert_force_close(acc, a_ref, f"{name} variant {v}")
-        assert acc.tobytes() == split.tobytes(), f"variant {v}"
+        assert acc.tobytes() == packed.tobytes(), f"variant {v}"
 
 
 def test_plain_kernel_matches_oracle(small_case):
