@@ -913,6 +913,109 @@ def run_fof(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_step(args, rank, world, local_rank):
+    """One whole time step of the force split on the clustered 256^3 set:
+    sr_bin -> sr_force (short range) -> sr_pm_deposit + sr_pm_transform +
+    sr_pm_power (on-the-fly P(k)) -> sr_pm_force added onto the short-range
+    accelerations -> sr_kick -> sr_invariants.  Metric: particles per
+    second through the whole step."""
+    cfg, vols, vel_np, prm = make_inputs("clustered256", args.n_particles, world, rank)
+    (pos, box), = vols
+    n = len(pos)
+    ng = args.n_grid or int(round(n ** (1.0 / 3.0)))
+
+    import torch
+
+    from paper_1411_3396_b300 import PM, Plan, kick, launch_count
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    x = torch.from_numpy(pos).to(dev)
+    vel = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+    vel[:, :3] = torch.from_numpy(vel_np).to(dev).float()
+    acc = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    inv = torch.empty(7, dtype=torch.float64, device=dev)
+    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n)
+    pm = PM(ng, box, prm["sigma"], n)
+    dt = prm["dt"]
+    plan.bin(x)
+    if args.variant >= 0:
+        plan.set_variant(args.variant)
+    else:
+        plan.autotune(reps=1)
+    _, pairs_t, _ = plan.force(acc, count=True)
+    torch.cuda.synchronize()
+    pairs = int(pairs_t.item())
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        plan.bin(x)
+        plan.force(acc)
+        if ev is not None:
+            ev[1].record()
+        pm.deposit(x)
+        pk = pm.power()
+        pm.force(x, acc, accumulate=True)
+        if ev is not None:
+            ev[2].record()
+        kick(acc, vel, dt)
+        plan.invariants(vel, acc, inv)
+        return pk
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    uuid = str(getattr(props, "uuid", "")) if hasattr(props, "uuid") else ""
+    sampler = ClockSampler(uuid if rank == 0 else "")
+    if rank == 0 and not args.no_clocks:
+        sampler.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    t_start.record()
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record()
+    torch.cuda.synchronize()
+    l1 = launch_count()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
+    ms = t_start.elapsed_time(t_end) / args.steps
+    sr_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    lr_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    n_all, ms_max = reduce_over_ranks(n, ms, world, dev)
+    plan.status()
+    pm.close()
+    plan.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "whole force-split time step (binning, short-range pairs, PM with P(k), kick): particles/sec",
+        "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "step256", "catalogue": "clustered256 particles", "n_particles": n, "n_grid": ng,
+                   "box": box, "r_c": prm["rc"], "eps": prm["eps"], "sigma": prm["sigma"], "dt": dt,
+                   "short_range_ms": sr_ms, "long_range_ms": lr_ms, "pairs_per_step": pairs,
+                   "short_range_pairs_per_s": pairs / (sr_ms * 1e-3),
+                   "l2": "inputs larger than L2 (402 MB positions); no flush",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": None,
+        "e2e": None,
+        "gpu_launches": int(l1 - l0),
+        "clocks": clocks,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_centers(args, rank, world):
     pos, box, lab, nh, eps = _centers_inputs(args.n_particles)
     if rank != 0:
@@ -1121,6 +1224,8 @@ def main():
         run_pm(args, rank, world, local_rank)
     elif args.workload == "fof256":
         run_fof(args, rank, world, local_rank)
+    elif args.workload == "step256":
+        run_step(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:
