@@ -1016,6 +1016,48 @@ def run_step(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_other(args, rank, world):
+    """Reference arm of the pm256, fof256 and step256 modes: the FP64
+    oracle of the same step on a bounded sample of the same catalogue."""
+    if rank != 0:
+        return
+    from oracle import fit as ofit
+    from oracle import force as oforce
+    from oracle import pm as opm
+    per = []
+    sample_n = 32 ** 3 if args.workload == "step256" else 64 ** 3
+    for k in range(args.warmup + args.steps):
+        if args.workload == "pm256":
+            rate, cn, _ = cpu_pm_sample(sample_n)
+        elif args.workload == "fof256":
+            rate, cn, _ = cpu_fof_sample(sample_n, args.fof_b)
+        else:
+            pos, box, sigma = _pm_inputs(sample_n)
+            from workloads import configs as wc
+            prm = wc.CONFIGS["clustered256"]
+            c = ofit.fit_poly(prm["rc"], sigma, prm["eps"])
+            t0 = time.perf_counter()
+            oforce.accel_kdtree(pos, box, prm["rc"], prm["eps"], c)
+            opm.power_spectrum(pos, box, int(round(len(pos) ** (1 / 3))))
+            opm.pm_accel(pos, box, int(round(len(pos) ** (1 / 3))), sigma)
+            cn = len(pos)
+            rate = cn / (time.perf_counter() - t0)
+        per.append(rate)
+    value = float(np.mean(per[args.warmup:]))
+    line = {
+        "impl": "reference", "metric": f"{args.workload} step (oracle FP64): particles/sec",
+        "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "catalogue": "clustered256 resized", "sample_particles": sample_n},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step the whole oracle step on the clustered catalogue resized to "
+                                   f"{sample_n} particles"},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_centers(args, rank, world):
     pos, box, lab, nh, eps = _centers_inputs(args.n_particles)
     if rank != 0:
@@ -1208,6 +1250,8 @@ def main():
         if rank == 0:
             if args.workload == "centers256":
                 run_reference_centers(args, rank, world)
+            elif args.workload in ("pm256", "fof256", "step256"):
+                run_reference_other(args, rank, world)
             else:
                 run_reference(args, rank, world)
         return
