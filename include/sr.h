@@ -47,6 +47,7 @@ extern "C" {
 #define SR_ERR_CAPACITY  3   /* n exceeds the plan's capacity */
 #define SR_ERR_STATE     4   /* call order violated (e.g. sr_force before sr_bin) */
 #define SR_ERR_RANGE     5   /* a position was non-finite or outside [-L, 2L) */
+#define SR_ERR_TIMEOUT   6   /* a bounded device-side loop ran out of iterations (see the call) */
 
 /* Polynomial fit modes. */
 #define SR_FIT_CONSTRAINED    0  /* least squares with p(r_c^2) = (r_c^2+eps^2)^(-3/2): f_SR(r_c^2) = 0 */

@@ -74,9 +74,19 @@ int sr_fof_run(sr_fof* f, sr_plan* plan, const double* pos, int64_t n, double li
 
 /*
  * sr_fof_get_info -- counts of the last run; synchronises its stream.
- * Errors: SR_ERR_ARG, SR_ERR_STATE (no run yet).
+ * Errors: SR_ERR_ARG, SR_ERR_STATE (no run yet), SR_ERR_TIMEOUT (out is
+ * filled; a union-find loop of that run reached its iteration limit, the
+ * labels are not valid; the workspace stays usable).
  */
 int sr_fof_get_info(sr_fof* f, sr_fof_info* out);
+
+/*
+ * sr_fof_set_iteration_limit -- bound of every union-find loop of later
+ * runs (0 restores the default, 2^24).  A small limit makes the loops run
+ * out on purpose, which exercises the timeout path without any device
+ * fault.  Errors: SR_ERR_ARG (null, negative).
+ */
+int sr_fof_set_iteration_limit(sr_fof* f, int64_t max_iter);
 
 #ifdef __cplusplus
 }

@@ -7,7 +7,7 @@ from ctypes import POINTER, c_double, c_float, c_int, c_int64, c_uint64, c_void_
 
 from .build import LIB
 
-SR_OK, SR_ERR_ARG, SR_ERR_CUDA, SR_ERR_CAPACITY, SR_ERR_STATE, SR_ERR_RANGE = range(6)
+SR_OK, SR_ERR_ARG, SR_ERR_CUDA, SR_ERR_CAPACITY, SR_ERR_STATE, SR_ERR_RANGE, SR_ERR_TIMEOUT = range(7)
 FIT_MODES = {"constrained": 0, "unconstrained": 1}
 EXPORTS = {
     "perm": 0, "cell_start": 1, "cell_chunk_start": 2, "slot_pos": 3, "slot_idx": 4,
@@ -95,6 +95,7 @@ SIGNATURES = {
     "sr_fof_destroy": (c_int, [c_void_p]),
     "sr_fof_run": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, c_int, c_void_p, c_void_p, c_void_p]),
     "sr_fof_get_info": (c_int, [c_void_p, POINTER(SrFofInfo)]),
+    "sr_fof_set_iteration_limit": (c_int, [c_void_p, c_int64]),
     "sr_last_error": (c_char_p, []),
     "sr_launch_count": (c_int64, []),
 }

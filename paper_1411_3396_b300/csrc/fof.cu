@@ -12,7 +12,8 @@
 //    sequence of the definition.  Friends are joined in a lock-free
 //    union-find: find with path halving, link by CAS of the larger root
 //    under the smaller, retried until the roots agree.  Every loop has an
-//    iteration bound that sets an error flag instead of spinning on.
+//    iteration bound (2^24 unless the caller sets another) that sets an
+//    error flag instead of spinning on; the host reads it as SR_ERR_TIMEOUT.
 // 3. Roots (the smallest index of each group) and group sizes; a scan over
 //    the roots of groups with at least min_members particles numbers the
 //    halos in increasing root order; labels in caller order.
@@ -25,7 +26,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFofThreads = 256;
-constexpr int kMaxIter = 1 << 24;
+constexpr long long kDefaultMaxIter = 1 << 24;   // default bound of every union-find loop
 constexpr double kBand = 1.0 / 1024.0;    // relative band of link^2 sent to the binary64 test
 
 struct FofCtr {
@@ -71,8 +72,8 @@ __device__ bool friends_exact(const double* __restrict__ pos, int i, int j, doub
 // Root of x.  Parent pointers only ever move to smaller indices (to an
 // ancestor), so the halving store is safe against concurrent finds and
 // links; loads bypass L1 so that a link made on another SM is seen.
-__device__ int find_root(int* parent, int x, FofCtr* c) {
-    for (int it = 0; it < kMaxIter; ++it) {
+__device__ int find_root(int* parent, int x, FofCtr* c, long long max_iter) {
+    for (long long it = 0; it < max_iter; ++it) {
         const int p = __ldcg(parent + x);
         if (p == x) return x;
         const int gp = __ldcg(parent + p);
@@ -83,9 +84,9 @@ __device__ int find_root(int* parent, int x, FofCtr* c) {
     return x;
 }
 
-__device__ void unite(int* parent, int a, int b, FofCtr* c) {
-    for (int it = 0; it < kMaxIter; ++it) {
-        const int ra = find_root(parent, a, c), rb = find_root(parent, b, c);
+__device__ void unite(int* parent, int a, int b, FofCtr* c, long long max_iter) {
+    for (long long it = 0; it < max_iter; ++it) {
+        const int ra = find_root(parent, a, c, max_iter), rb = find_root(parent, b, c, max_iter);
         if (ra == rb) return;
         const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
         if (atomicCAS(parent + hi, hi, lo) == hi) return;
@@ -107,7 +108,8 @@ __global__ void __launch_bounds__(kFofThreads)
 k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict__ meta,
             const float4* __restrict__ clo, const float4* __restrict__ chi, const float4* __restrict__ slot_pos,
             const int* __restrict__ slot_idx, const sr::VolDev* __restrict__ vols, const int* __restrict__ order,
-            const double* __restrict__ pos, double link, double link2, int* parent, FofCtr* c) {
+            const double* __restrict__ pos, double link, double link2, int* parent, FofCtr* c,
+            long long max_iter) {
     constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
     const int n_items = ccs[total_cells];
@@ -136,7 +138,7 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
             ii[k] = slot_idx[(long long)I * C + lane + 32 * k];
             // an ancestor of the particle's group root: a friend whose root
             // equals it is already joined
-            ri[k] = ii[k] >= 0 ? find_root(parent, ii[k], c) : -1;
+            ri[k] = ii[k] >= 0 ? find_root(parent, ii[k], c, max_iter) : -1;
         }
         const int b = V.sub_bits;
         int cc[3], olo[3], ohi[3];
@@ -212,9 +214,9 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
                                             }
                                             if (f) {
                                                 ++my_links;
-                                                if (find_root(parent, jidx, c) != ri[k]) {
-                                                    unite(parent, ii[k], jidx, c);
-                                                    ri[k] = find_root(parent, ii[k], c);
+                                                if (find_root(parent, jidx, c, max_iter) != ri[k]) {
+                                                    unite(parent, ii[k], jidx, c, max_iter);
+                                                    ri[k] = find_root(parent, ii[k], c, max_iter);
                                                 }
                                             }
                                         }
@@ -240,10 +242,11 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
     }
 }
 
-__global__ void k_fof_roots(int n, int* parent, int* __restrict__ root, int* __restrict__ size, FofCtr* c) {
+__global__ void k_fof_roots(int n, int* parent, int* __restrict__ root, int* __restrict__ size, FofCtr* c,
+                            long long max_iter) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int r = find_root(parent, i, c);
+    const int r = find_root(parent, i, c, max_iter);
     root[i] = r;
     atomicAdd(&size[r], 1);
 }
@@ -279,6 +282,7 @@ inline unsigned grid_for(long long n, int threads) {
 
 struct sr_fof {
     long long n_max = 0;
+    long long max_iter = kDefaultMaxIter;
     int* parent = nullptr;
     int* root = nullptr;
     int* size = nullptr;
@@ -365,13 +369,13 @@ int sr_fof_run(sr_fof* f, sr_plan* p, const double* pos, int64_t n, double link,
         if (p->chunk_k == 2)
             k_fof_pairs<2><<<f->blocks[1], kFofThreads, 0, st>>>(
                 p->ccs, (int)p->total_cells, p->chunk_meta, p->chunk_lo, p->chunk_hi, p->slot_pos, p->slot_idx,
-                p->vols, p->order, pos, link, link * link, f->parent, f->ctr);
+                p->vols, p->order, pos, link, link * link, f->parent, f->ctr, f->max_iter);
         else
             k_fof_pairs<1><<<f->blocks[0], kFofThreads, 0, st>>>(
                 p->ccs, (int)p->total_cells, p->chunk_meta, p->chunk_lo, p->chunk_hi, p->slot_pos, p->slot_idx,
-                p->vols, p->order, pos, link, link * link, f->parent, f->ctr);
+                p->vols, p->order, pos, link, link * link, f->parent, f->ctr, f->max_iter);
         SR_LAUNCH_CHECK("k_fof_pairs");
-        k_fof_roots<<<grid_for(N, 256), 256, 0, st>>>(N, f->parent, f->root, f->size, f->ctr);
+        k_fof_roots<<<grid_for(N, 256), 256, 0, st>>>(N, f->parent, f->root, f->size, f->ctr, f->max_iter);
         SR_LAUNCH_CHECK("k_fof_roots");
     }
     k_fof_flags<<<grid_for((long long)N + 1, 256), 256, 0, st>>>(N, min_members, f->root, f->size, f->flag);
@@ -386,6 +390,13 @@ int sr_fof_run(sr_fof* f, sr_plan* p, const double* pos, int64_t n, double link,
     f->ran = true;
     f->last_n = n;
     f->last_stream = st;
+    return SR_OK;
+}
+
+int sr_fof_set_iteration_limit(sr_fof* f, int64_t max_iter) {
+    if (!f) return sr::set_error(SR_ERR_ARG, "sr_fof_set_iteration_limit: null workspace");
+    if (max_iter < 0) return sr::set_error(SR_ERR_ARG, "sr_fof_set_iteration_limit: negative limit");
+    f->max_iter = max_iter == 0 ? kDefaultMaxIter : max_iter;
     return SR_OK;
 }
 
@@ -405,6 +416,8 @@ int sr_fof_get_info(sr_fof* f, sr_fof_info* out) {
     out->band_checks = (int64_t)h.band;
     out->tests = (int64_t)h.tests;
     out->error = h.err ? 1 : 0;
+    if (h.err)
+        return sr::set_error(SR_ERR_TIMEOUT, "sr_fof_run: a union-find loop reached its iteration limit; labels invalid");
     return SR_OK;
 }
 

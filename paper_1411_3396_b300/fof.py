@@ -50,7 +50,14 @@ class FOF:
                                 _ptr(labels), _ptr(halo_sizes), _stream()))
         return labels, halo_sizes
 
+    def set_iteration_limit(self, max_iter: int = 0):
+        """Bound of the union-find loops (0 = default); a tiny bound makes
+        them run out, which get_info reports as SR_ERR_TIMEOUT."""
+        check(load().sr_fof_set_iteration_limit(self._h, int(max_iter)))
+
     def info(self) -> dict:
+        """Counts of the last run; raises SrError (SR_ERR_TIMEOUT) if a
+        union-find loop ran out of iterations."""
         inf = SrFofInfo()
         check(load().sr_fof_get_info(self._h, byref(inf)))
         return {k: getattr(inf, k) for k, _ in SrFofInfo._fields_}

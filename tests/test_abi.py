@@ -135,5 +135,8 @@ def test_fof_argument_checks_need_no_device(lib):
     assert run(None, None, None, 0, 0.2, 40, None, None, None) == 1
     lib.sr_fof_get_info.restype = ctypes.c_int
     assert lib.sr_fof_get_info(None, None) == 1
+    lib.sr_fof_set_iteration_limit.restype = ctypes.c_int
+    lib.sr_fof_set_iteration_limit.argtypes = [v, ctypes.c_int64]
+    assert lib.sr_fof_set_iteration_limit(None, 5) == 1
     lib.sr_fof_destroy.restype = ctypes.c_int
     assert lib.sr_fof_destroy(None) == 0

@@ -146,3 +146,29 @@ def test_full_clustered_256_closure():
         assert np.all(lab[fr] == lab[i]) or (lab[i] == -1 and np.all(lab[fr] == -1))
     print(f"256^3 FOF b=0.168: {info['n_halos']} halos, {info['n_members']} members, "
           f"largest {info['max_members']}, {info['links']} links")
+
+
+def test_iteration_limit_reports_timeout_and_workspace_recovers():
+    # the union-find loops run out on purpose (limit 1): the run returns,
+    # the host reads SR_ERR_TIMEOUT, and the next run with the default limit
+    # is exact again; nothing faults or hangs on the device
+    from paper_1411_3396_b300 import FOF, SrError
+    from paper_1411_3396_b300._lib import SR_ERR_TIMEOUT
+    w = wc.make_workload(wc.small_variant("clustered256"))
+    (pos, box), = w["volumes"]
+    plan = make_plan(w["volumes"], PARAMS)
+    x = torch.from_numpy(pos).cuda()
+    plan.bin(x)
+    f = FOF(len(pos))
+    f.set_iteration_limit(1)
+    f.run(plan, x, 0.2, 40)
+    with pytest.raises(SrError) as e:
+        f.info()
+    assert e.value.code == SR_ERR_TIMEOUT
+    f.set_iteration_limit(0)
+    lab, _ = f.run(plan, x, 0.2, 40)
+    info = f.info()
+    assert info["error"] == 0
+    np.testing.assert_array_equal(lab.cpu().numpy(), ofof.fof(pos, box, 0.2, 40)[0])
+    f.close()
+    plan.close()
