@@ -1,0 +1,136 @@
+"""Slab decomposition of one periodic volume over ranks with an overload
+(ghost) shell, after the paper's overloading scheme (Sec. 2, Sec. 2.1):
+every rank owns the particles of a slab of whole cells along x and, before
+the force, receives from the other ranks the particles of the cells next to
+its slab (periodic in x).  Each rank bins its owned and ghost particles in a
+plan of the whole box (same side, same cells, so the cells away from its
+slab are simply empty) and keeps the forces of its owned particles only;
+ghosts are read-only, so no reduction follows.
+
+Cells are at least r_c wide and the pair kernel reads only the 27 cells
+around a particle's own, so one ghost cell on each side of the slab holds
+every neighbour within r_c.  Cell membership here follows the binning
+kernel's definition exactly (fold into [0, L), t = x / h in binary64,
+q = min(floor(t), M - 1), cell = q >> b), and the local particles are kept
+in increasing global-id order; the binning sort is stable, so every cell an
+owned particle reads holds the same particles in the same order as in the
+undivided volume, and the owned particles' forces are bit-identical to the
+single-volume result.
+
+Index bookkeeping (cells, masks, selection, ordering) runs in PyTorch on the
+tensors' device, and the exchange in torch.distributed (gloo or NCCL); this
+is orchestration around the library's kernels, not part of the force
+arithmetic.
+"""
+from __future__ import annotations
+
+import torch
+
+
+def slab_bounds(n_cells: int, world: int):
+    """Cell-index ranges [c0, c1) along x of each rank (as even as possible)."""
+    if world < 1 or world > n_cells:
+        raise ValueError("need 1 <= world <= n_cells")
+    base, extra = divmod(n_cells, world)
+    out, c = [], 0
+    for r in range(world):
+        w = base + (1 if r < extra else 0)
+        out.append((c, c + w))
+        c += w
+    return out
+
+
+class Slabs:
+    """x-slabs of whole cells of one periodic volume of side `box` with
+    `n_cells` cells per axis, each split into 2^sub_bits fine cells of side
+    h = box / (n_cells 2^sub_bits) (the binning's grid)."""
+
+    def __init__(self, box: float, n_cells: int, sub_bits: int, world: int):
+        self.box = float(box)
+        self.n_cells = int(n_cells)
+        self.sub_bits = int(sub_bits)
+        self.M = self.n_cells << self.sub_bits
+        self.h = self.box / self.M
+        self.world = int(world)
+        self.bounds = slab_bounds(self.n_cells, self.world)
+
+    @classmethod
+    def of_plan(cls, plan, world: int, volume: int = 0):
+        """Slabs on the cell grid of a plan's volume."""
+        v = plan.volume(volume)
+        return cls(v["box"], v["n_cells"], plan.info()["sub_bits"], world)
+
+    def cell_x(self, pos: torch.Tensor) -> torch.Tensor:
+        """Cell index along x of every particle (the binning's definition)."""
+        x = pos[:, 0]
+        x = torch.where(x < 0, x + self.box, x)
+        x = torch.where(x >= self.box, x - self.box, x)
+        q = torch.clamp(torch.floor(x / self.h), max=self.M - 1).to(torch.int64)
+        return q >> self.sub_bits
+
+    def owned(self, pos: torch.Tensor, rank: int) -> torch.Tensor:
+        """Mask of the particles in rank's slab."""
+        c0, c1 = self.bounds[rank]
+        cx = self.cell_x(pos)
+        return (cx >= c0) & (cx < c1)
+
+    def ghost(self, pos: torch.Tensor, rank: int) -> torch.Tensor:
+        """Mask of the particles outside rank's slab in the cells next to
+        it (c0 - 1 and c1, periodically)."""
+        c0, c1 = self.bounds[rank]
+        cx = self.cell_x(pos)
+        inside = (cx >= c0) & (cx < c1)
+        near = (cx == (c0 - 1) % self.n_cells) | (cx == c1 % self.n_cells)
+        return near & ~inside
+
+    def local_set(self, pos: torch.Tensor, ids: torch.Tensor, rank: int):
+        """Owned and ghost particles of `rank` drawn from one array holding
+        every particle: (positions, global ids, owned flags) in increasing
+        global-id order."""
+        own = self.owned(pos, rank)
+        sel = torch.nonzero(own | self.ghost(pos, rank)).squeeze(1)
+        sel = sel[torch.argsort(ids[sel])]
+        return pos[sel].contiguous(), ids[sel].contiguous(), own[sel].contiguous()
+
+    def exchange(self, pos: torch.Tensor, ids: torch.Tensor, group=None):
+        """Overload exchange between ranks that each hold exactly their owned
+        particles (pos, ids): returns this rank's owned + ghost particles
+        (positions, global ids, owned flags) in increasing global-id order.
+        One all-gather of the send counts, then point-to-point sends to
+        every rank of the particles in the cells next to its slab."""
+        import torch.distributed as dist
+        world = dist.get_world_size(group)
+        rank = dist.get_rank(group)
+        if world != self.world:
+            raise ValueError("slab count differs from the process group size")
+        dev = pos.device
+        sends = [None if q == rank else torch.nonzero(self.ghost(pos, q)).squeeze(1)
+                 for q in range(world)]
+        counts = torch.tensor([0 if s is None else len(s) for s in sends], dtype=torch.int64, device=dev)
+        table = [torch.zeros_like(counts) for _ in range(world)]
+        dist.all_gather(table, counts, group=group)
+        recv_pos, recv_ids, reqs = [], [], []
+        for q in range(world):
+            if q == rank:
+                continue
+            nq = int(table[q][rank].item())
+            rp = torch.empty((nq, 3), dtype=pos.dtype, device=dev)
+            ri = torch.empty(nq, dtype=ids.dtype, device=dev)
+            recv_pos.append(rp)
+            recv_ids.append(ri)
+            if nq:
+                reqs.append(dist.irecv(rp, src=q, group=group, tag=2 * q))
+                reqs.append(dist.irecv(ri, src=q, group=group, tag=2 * q + 1))
+        for q in range(world):
+            if q == rank or len(sends[q]) == 0:
+                continue
+            reqs.append(dist.isend(pos[sends[q]].contiguous(), dst=q, group=group, tag=2 * rank))
+            reqs.append(dist.isend(ids[sends[q]].contiguous(), dst=q, group=group, tag=2 * rank + 1))
+        for r in reqs:
+            r.wait()
+        all_pos = torch.cat([pos] + recv_pos)
+        all_ids = torch.cat([ids] + recv_ids)
+        own = torch.cat([torch.ones(len(pos), dtype=torch.bool, device=dev)] +
+                        [torch.zeros(len(r), dtype=torch.bool, device=dev) for r in recv_ids])
+        order = torch.argsort(all_ids)
+        return all_pos[order].contiguous(), all_ids[order].contiguous(), own[order].contiguous()

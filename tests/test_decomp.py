@@ -1,0 +1,122 @@
+"""Host logic of the overload slab decomposition (Sec. 2, Sec. 2.1) on CPU:
+slab bounds, cell membership against the oracle's binning, owned sets that
+partition the volume, ghost shells of exactly the neighbouring cells, and the
+point-to-point exchange between gloo ranks (world sizes 2 and 3), which must
+hand every rank the same owned + ghost set as a selection from the whole
+array."""
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import binning as obin
+from workloads import generators as gen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _clustered(n=6000, box=24.0, seed=5):
+    pos, _, _ = gen.nfw_clustered(n, box, seed, m_lo=40.0, m_hi=600.0)
+    pos[:7, 0] = [0.0, box / 8 * 3, -1e-12, box - 1e-12, 3.0 * box / 8, 1.5 * box, -0.5 * box]
+    return pos
+
+
+def test_slab_bounds_partition():
+    from paper_1411_3396_b300.decomp import slab_bounds
+    for n_c in (1, 3, 7, 64):
+        for world in range(1, min(n_c, 9) + 1):
+            b = slab_bounds(n_c, world)
+            assert b[0][0] == 0 and b[-1][1] == n_c
+            assert all(b[r][1] == b[r + 1][0] for r in range(world - 1))
+            w = [c1 - c0 for c0, c1 in b]
+            assert min(w) >= 1 and max(w) - min(w) <= 1
+    with pytest.raises(ValueError):
+        slab_bounds(4, 5)
+    with pytest.raises(ValueError):
+        slab_bounds(4, 0)
+
+
+@pytest.mark.parametrize("n_c,b", [(8, 0), (6, 2), (5, 3)])
+def test_cells_follow_the_binning(n_c, b):
+    from paper_1411_3396_b300.decomp import Slabs
+    box = 24.0
+    pos = _clustered(box=box)
+    s = Slabs(box, n_c, b, 3)
+    _, q = obin.fine_coords(pos, box, n_c, b)
+    np.testing.assert_array_equal(s.cell_x(torch.from_numpy(pos)).numpy(), q[:, 0] >> b)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+def test_owned_partition_and_ghost_shell(world):
+    from paper_1411_3396_b300.decomp import Slabs
+    box, n_c = 24.0, 6
+    pos = _clustered(box=box)
+    x = torch.from_numpy(pos)
+    s = Slabs(box, n_c, 1, world)
+    _, q = obin.fine_coords(pos, box, n_c, 1)
+    cx = q[:, 0] >> 1
+    owners = np.zeros(len(pos), dtype=np.int64)
+    for r in range(world):
+        own = s.owned(x, r).numpy()
+        owners += own
+        c0, c1 = s.bounds[r]
+        ghost = s.ghost(x, r).numpy()
+        assert not np.any(own & ghost)
+        want = np.isin(cx, [(c0 - 1) % n_c, c1 % n_c]) & ~((cx >= c0) & (cx < c1))
+        np.testing.assert_array_equal(ghost, want)
+        p, ids, flag = s.local_set(x, torch.arange(len(pos)), r)
+        assert torch.all(ids[1:] > ids[:-1])
+        np.testing.assert_array_equal(flag.numpy(), own[ids.numpy()])
+        np.testing.assert_array_equal(p.numpy(), pos[ids.numpy()])
+    np.testing.assert_array_equal(owners, np.ones(len(pos), dtype=np.int64))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    from paper_1411_3396_b300.decomp import Slabs
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        box = 24.0
+        pos = torch.from_numpy(_clustered(box=box))
+        ids = torch.arange(len(pos), dtype=torch.int64)
+        s = Slabs(box, 6, 0, world)
+        mine = s.owned(pos, rank)
+        # every rank starts with its owned particles only, in a scrambled order
+        perm = torch.randperm(int(mine.sum()), generator=torch.Generator().manual_seed(rank))
+        p0, i0 = pos[mine][perm], ids[mine][perm]
+        got = s.exchange(p0, i0)
+        want = s.local_set(pos, ids, rank)
+        ok = all(torch.equal(a, b) for a, b in zip(got, want))
+        q.put((rank, ok, int(got[2].sum()), len(got[1])))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_exchange_gloo(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok, _, _ in res)
+    assert sum(n_own for _, _, n_own, _ in res) == 6000
+    assert all(n_loc > n_own for _, _, n_own, n_loc in res)

@@ -1,0 +1,79 @@
+"""Overload slab decomposition (Sec. 2, Sec. 2.1) on the GPU: every rank's
+owned + ghost set is binned in a plan of the whole box and forced; the
+owned particles' accelerations and pair counts must be bit-identical to the
+undivided volume's, and within the force tolerance of the oracle.  The
+ranks' sub-problems run one after another on one device (independent
+launches, no rank waits on another)."""
+import numpy as np
+import pytest
+
+from workloads import configs as wc
+
+from helpers import assert_force_close, oracle_force, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _force(pos, box, prm, n_cells, chunk):
+    from paper_1411_3396_b300 import Plan
+    plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], len(pos), n_cells=n_cells, chunk_size=chunk)
+    plan.bin(pos)
+    acc, pairs, pp = plan.force(count=True, per_particle=True)
+    torch.cuda.synchronize()
+    return plan, acc, int(pairs.item()), pp
+
+
+def _check_ranks(pos_np, box, prm, world, chunk):
+    from paper_1411_3396_b300.decomp import Slabs
+    pos = torch.from_numpy(pos_np).cuda()
+    plan, acc_full, pairs_full, pp_full = _force(pos, box, prm, 0, chunk)
+    slabs = Slabs.of_plan(plan, world)
+    n_c = plan.volume(0)["n_cells"]
+    assert slabs.h == plan.volume(0)["h"]
+    plan.close()
+    ids_all = torch.arange(len(pos), device="cuda")
+    seen = torch.zeros(len(pos), dtype=torch.int32, device="cuda")
+    pairs_owned = 0
+    for r in range(world):
+        p, ids, own = slabs.local_set(pos, ids_all, r)
+        pl, acc, _, pp = _force(p, box, prm, n_c, chunk)
+        pl.close()
+        mine = ids[own]
+        assert torch.equal(acc[own], acc_full[mine]), f"rank {r}: forces differ from the whole volume"
+        assert torch.equal(pp[own], pp_full[mine])
+        seen[mine] += 1
+        pairs_owned += int(pp[own].sum().item())
+    assert torch.all(seen == 1)
+    assert pairs_owned == pairs_full
+    return to_np(acc_full)
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_clustered_slabs_bit_identical(world, chunk):
+    w = wc.make_workload(wc.small_variant("clustered256"))
+    (pos, box), = w["volumes"]
+    acc = _check_ranks(pos, box, w["params"], world, chunk)
+    a_ref, _ = oracle_force(w["volumes"], w["params"])
+    assert_force_close(acc, a_ref, f"slabs {world}")
+
+
+def test_zeldovich_slabs_with_positions_outside_the_box():
+    # unwrapped positions in [-L, 2L): slab membership follows the same fold
+    w = wc.make_workload(wc.small_variant("zeldovich128"))
+    (pos, box), = w["volumes"]
+    pos = pos.copy()
+    rng = np.random.default_rng(11)
+    shift = rng.choice([-1.0, 0.0, 1.0], size=pos.shape) * box
+    pos = pos + shift
+    pos = np.where(pos < -box, pos + box, pos)
+    pos = np.where(pos >= 2 * box, pos - box, pos)
+    _check_ranks(pos, box, w["params"], 3, 32)
+
+
+def test_full_clustered_256_four_slabs():
+    w = wc.make_workload(wc.CONFIGS["clustered256"])
+    (pos, box), = w["volumes"]
+    _check_ranks(pos, box, w["params"], 4, 32)
