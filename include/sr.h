@@ -300,8 +300,11 @@ int sr_plan_copy(sr_plan* plan, int which, void* dst, int64_t bytes, void* strea
  * sr_step_host -- one whole step from host buffers (end-to-end form): copy
  * pos (host binary64 rows) and vel (host float4 rows) to plan-owned device
  * buffers, sr_bin, sr_force_kick, copy acc (host float4 rows, nullable)
- * and the updated vel back, and wait for completion.  Host buffers should be
- * page-locked for overlap.  The first call allocates the staging buffers.
+ * and the updated vel back, and wait for completion.  The velocity upload
+ * runs on a plan-owned side stream after the position upload, beside the
+ * binning (the force waits for it).  Host buffers should be page-locked for
+ * overlap.  The first call allocates the staging buffers, the side stream
+ * and two events.
  */
 int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float dt,
                  int64_t n, void* stream);

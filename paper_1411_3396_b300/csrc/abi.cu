@@ -55,6 +55,9 @@ void free_plan(sr_plan* p) {
     cudaFree(p->h_pos_dev);
     cudaFree(p->h_vel_dev);
     cudaFree(p->h_acc_dev);
+    if (p->h_side) cudaStreamDestroy(p->h_side);
+    if (p->h_fork) cudaEventDestroy(p->h_fork);
+    if (p->h_join) cudaEventDestroy(p->h_join);
     radix_free(p->rs_particles);
     radix_free(p->rs_chunks);
     scan_free(p->scan_cells);
@@ -460,9 +463,24 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
             (rc = dalloc(&p->h_acc_dev, (size_t)p->capacity * 4)))
             return rc;
     }
+    if (!p->h_side) {
+        SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->h_side, cudaStreamNonBlocking));
+        SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->h_fork, cudaEventDisableTiming));
+        SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->h_join, cudaEventDisableTiming));
+    }
+    // The velocity upload runs on a side stream after the position upload
+    // (both share the host link, and the binning needs the positions first),
+    // beside the binning; the force kernel (which reads the velocities in the
+    // fused kick) waits for it.
     SR_CUDA_CHECK(cudaMemcpyAsync(p->h_pos_dev, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-    SR_CUDA_CHECK(cudaMemcpyAsync(p->h_vel_dev, vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, st));
-    if ((rc = sr_bin(p, p->h_pos_dev, n, stream))) return rc;
+    SR_CUDA_CHECK(cudaEventRecord(p->h_fork, st));
+    SR_CUDA_CHECK(cudaStreamWaitEvent(p->h_side, p->h_fork, 0));
+    SR_CUDA_CHECK(cudaMemcpyAsync(p->h_vel_dev, vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, p->h_side));
+    SR_CUDA_CHECK(cudaEventRecord(p->h_join, p->h_side));
+    rc = sr_bin(p, p->h_pos_dev, n, stream);
+    cudaError_t we = cudaStreamWaitEvent(st, p->h_join, 0);       // join even when sr_bin failed
+    if (rc) return rc;
+    if (we != cudaSuccess) return cuda_fail(we, "sr_step_host");
     if ((rc = launch_force(p, p->h_acc_dev, nullptr, nullptr, st, p->h_vel_dev, dt))) return rc;
     SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->h_vel_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
     if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));

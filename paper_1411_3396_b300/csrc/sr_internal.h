@@ -119,6 +119,8 @@ struct sr_plan {
     double* h_pos_dev = nullptr;
     float* h_vel_dev = nullptr;
     float* h_acc_dev = nullptr;
+    cudaStream_t h_side = nullptr;      // sr_step_host: velocity upload beside the binning
+    cudaEvent_t h_fork = nullptr, h_join = nullptr;
 
     int sm_count = 0;
     int variant = 0;                       // pair-kernel variant (launch bounds), see force.cu

@@ -119,15 +119,19 @@ def test_step_host_matches_device_path():
     plan = make_plan(w["volumes"], prm)
     vh = torch.from_numpy(v0.copy()).pin_memory()
     ah = torch.empty((n, 4), dtype=torch.float32).pin_memory()
-    plan.step_host(torch.from_numpy(pos).pin_memory(), vh, ah, prm["dt"])
     dev = make_plan(w["volumes"], prm)
-    dev.bin(torch.from_numpy(pos).cuda())
-    acc = dev.force()
     vd = torch.from_numpy(v0.copy()).cuda()
     from paper_1411_3396_b300 import kick
-    kick(acc, vd, prm["dt"])
-    assert ah.numpy().tobytes() == to_np(acc).tobytes()
-    assert vh.numpy().tobytes() == to_np(vd).tobytes()
+    # two consecutive steps (the second from moved positions): the side-stream
+    # velocity upload must see the first step's kicked velocities
+    for step in range(2):
+        p = pos if step == 0 else np.mod(pos + 0.3 * v0[:, :3].astype(np.float64), box)
+        plan.step_host(torch.from_numpy(p).pin_memory(), vh, ah, prm["dt"])
+        dev.bin(torch.from_numpy(p).cuda())
+        acc = dev.force()
+        kick(acc, vd, prm["dt"])
+        assert ah.numpy().tobytes() == to_np(acc).tobytes()
+        assert vh.numpy().tobytes() == to_np(vd).tobytes()
 
 
 def test_batch_full_size_graph_and_sampled_oracle():
