@@ -4,14 +4,21 @@
 // 2. k_fof_pairs: persistent warps take the plan's chunks in its cost order;
 //    for chunk I, the neighbour cells its box comes within the linking
 //    length of, and in them the chunks J >= I whose boxes do (each
-//    unordered chunk pair once; inside I only slot pairs i < j).  Lane i
-//    tests its particle against the 32 (or 64) slots of J, broadcast by
-//    shuffles, with a binary32 predicate in fine-grid units (exact integer
+//    unordered chunk pair once; inside I only slot pairs i < j).  Each lane
+//    first tests its slot of J against I's box (the same margined radius),
+//    and lane i then tests its particle against the surviving slots of J,
+//    broadcast by shuffles, with a binary32 predicate in fine-grid units (exact integer
 //    shifts between chunk anchors); pairs within a relative 2^-10 of link^2
 //    are decided again from the binary64 positions with the exact rounding
-//    sequence of the definition.  Friends are joined in a lock-free
-//    union-find: find with path halving, link by CAS of the larger root
-//    under the smaller, retried until the roots agree.  Every loop has an
+//    sequence of the definition.  Each friend pair found is appended to a
+//    per-warp link buffer in shared memory (as the lane's cached group root
+//    and the friend's index); when the buffer is nearly full, and at the end
+//    of every item, the 32 lanes resolve the buffered links together, so the
+//    union-find's memory round trips overlap instead of stalling the test
+//    loop one at a time.  The union-find is lock-free: find with path
+//    halving, link by CAS of the larger root under the smaller, retried
+//    until the roots agree, so the final roots (each group's smallest index)
+//    do not depend on the order of the links.  Every loop has an
 //    iteration bound (2^24 unless the caller sets another) that sets an
 //    error flag instead of spinning on; the host reads it as SR_ERR_TIMEOUT.
 // 3. Roots (the smallest index of each group) and group sizes; a scan over
@@ -26,6 +33,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFofThreads = 256;
+constexpr int kLinkCap = 256;              // per-warp link buffer (entries)
 constexpr long long kDefaultMaxIter = 1 << 24;   // default bound of every union-find loop
 constexpr double kBand = 1.0 / 1024.0;    // relative band of link^2 sent to the binary64 test
 
@@ -96,6 +104,25 @@ __device__ void unite(int* parent, int a, int b, FofCtr* c, long long max_iter) 
     atomicOr(&c->err, 1ull);
 }
 
+// The warp's buffered links (a, b) joined: lane l takes entries l, l + 32,
+// ...; nl <= kLinkCap.  a is a cached group root (an ancestor of it): when
+// b's root is a, the two are already in one group and nothing is written.
+// Then every lane's cached roots move up to the current roots.
+template <int K>
+__device__ __forceinline__ void flush_links(const int2* buf, int nl, int* parent, FofCtr* c, long long max_iter,
+                                            int (&ri)[K]) {
+    __syncwarp();
+    for (int e = (threadIdx.x & 31); e < nl; e += 32) {
+        const int2 l = buf[e];
+        const int rb = find_root(parent, l.y, c, max_iter);
+        if (rb != l.x) unite(parent, l.x, rb, c, max_iter);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if (ri[k] >= 0) ri[k] = find_root(parent, ri[k], c, max_iter);
+    __syncwarp();
+}
+
 __global__ void k_fof_init(int n, int* __restrict__ parent, int* __restrict__ size) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -104,14 +131,17 @@ __global__ void k_fof_init(int n, int* __restrict__ parent, int* __restrict__ si
 }
 
 template <int K>
-__global__ void __launch_bounds__(kFofThreads)
+__global__ void __launch_bounds__(kFofThreads, 4)
 k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict__ meta,
             const float4* __restrict__ clo, const float4* __restrict__ chi, const float4* __restrict__ slot_pos,
             const int* __restrict__ slot_idx, const sr::VolDev* __restrict__ vols, const int* __restrict__ order,
             const double* __restrict__ pos, double link, double link2, int* parent, FofCtr* c,
             long long max_iter) {
     constexpr int C = 32 * K;
+    __shared__ int2 links_buf[kFofThreads / 32][kLinkCap];
     const int lane = threadIdx.x & 31;
+    int2* lbuf = links_buf[threadIdx.x >> 5];
+    const unsigned lt = (1u << lane) - 1u;
     const int n_items = ccs[total_cells];
     unsigned long long my_links = 0, my_band = 0, my_tests = 0;
     while (true) {
@@ -136,10 +166,11 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
         for (int k = 0; k < K; ++k) {
             pi[k] = slot_pos[(long long)I * C + lane + 32 * k];
             ii[k] = slot_idx[(long long)I * C + lane + 32 * k];
-            // an ancestor of the particle's group root: a friend whose root
-            // equals it is already joined
+            // the particle's group root as last seen (an ancestor of it);
+            // links are buffered from it, which shortens their finds
             ri[k] = ii[k] >= 0 ? find_root(parent, ii[k], c, max_iter) : -1;
         }
+        int nl = 0;                                              // buffered links (warp-uniform)
         const int b = V.sub_bits;
         int cc[3], olo[3], ohi[3];
 #pragma unroll
@@ -193,7 +224,18 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
                             }
 #pragma unroll
                             for (int kk = 0; kk < K; ++kk) {
-                                for (int sl = 0; sl < 32; ++sl) {
+                                // particle cull: only slots of J within the (margined) linking
+                                // length of I's box can have a friend in I
+                                bool near = false;
+                                {
+                                    const float xj = pj[kk].x + sx, yj = pj[kk].y + sy, zj = pj[kk].z + sz;
+                                    const float gx = fmaxf(fmaxf(xj - ihi[0], ilo[0] - xj), 0.f);
+                                    const float gy = fmaxf(fmaxf(yj - ihi[1], ilo[1] - yj), 0.f);
+                                    const float gz = fmaxf(fmaxf(zj - ihi[2], ilo[2] - zj), 0.f);
+                                    near = jj[kk] >= 0 && gx * gx + gy * gy + gz * gz < cull2;
+                                }
+                                for (unsigned sm = __ballot_sync(kFull, near); sm; sm &= sm - 1) {
+                                    const int sl = __ffs(sm) - 1;
                                     const float xj = __shfl_sync(kFull, pj[kk].x, sl) + sx;
                                     const float yj = __shfl_sync(kFull, pj[kk].y, sl) + sy;
                                     const float zj = __shfl_sync(kFull, pj[kk].z, sl) + sz;
@@ -202,23 +244,28 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
 #pragma unroll
                                     for (int k = 0; k < K; ++k) {
                                         const int is = lane + 32 * k;
-                                        if (ii[k] < 0 || jidx < 0 || (Jl == I && js <= is)) continue;
-                                        ++my_tests;
-                                        const float dx = xj - pi[k].x, dy = yj - pi[k].y, dz = zj - pi[k].z;
-                                        const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                                        if (s < hi_thr) {
-                                            bool f = s < lo_thr;
-                                            if (!f) {
-                                                ++my_band;
-                                                f = friends_exact(pos, ii[k], jidx, V.box, link2);
-                                            }
-                                            if (f) {
-                                                ++my_links;
-                                                if (find_root(parent, jidx, c, max_iter) != ri[k]) {
-                                                    unite(parent, ii[k], jidx, c, max_iter);
-                                                    ri[k] = find_root(parent, ii[k], c, max_iter);
+                                        bool f = false;
+                                        if (ii[k] >= 0 && jidx >= 0 && !(Jl == I && js <= is)) {
+                                            ++my_tests;
+                                            const float dx = xj - pi[k].x, dy = yj - pi[k].y, dz = zj - pi[k].z;
+                                            const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                                            if (s < hi_thr) {
+                                                f = s < lo_thr;
+                                                if (!f) {
+                                                    ++my_band;
+                                                    f = friends_exact(pos, ii[k], jidx, V.box, link2);
                                                 }
                                             }
+                                        }
+                                        const unsigned fm = __ballot_sync(kFull, f);
+                                        if (f) {
+                                            ++my_links;
+                                            lbuf[nl + __popc(fm & lt)] = make_int2(ri[k], jidx);
+                                        }
+                                        nl += __popc(fm);
+                                        if (nl > kLinkCap - 32) {
+                                            flush_links<K>(lbuf, nl, parent, c, max_iter, ri);
+                                            nl = 0;
                                         }
                                     }
                                 }
@@ -228,6 +275,7 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
                 }
             }
         }
+        if (nl > 0) flush_links<K>(lbuf, nl, parent, c, max_iter, ri);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
