@@ -101,6 +101,7 @@ int make_volume(const sr_params& q, const double coef[6], int b, int cell_base, 
     int ex = 0;
     V->h_pow2 = (std::frexp(h, &ex) == 0.5) ? 1 : 0;
     V->inv_h = V->h_pow2 ? 1.0 / h : 0.0;
+    V->inv_h_exp = V->h_pow2 ? 1 - ex : 0;            // h = 2^(ex - 1)
     const double h2 = h * h;
     const double e64 = q.eps * q.eps;
     V->eps2u = (float)(e64 / h2);

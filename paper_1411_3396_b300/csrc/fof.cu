@@ -153,7 +153,7 @@ k_fof_pairs(const int* __restrict__ ccs, int total_cells, const int4* __restrict
         const int4 m = meta[I];
         const float4 lo = clo[I], hi = chi[I];
         const sr::VolDev& V = vols[m.w];
-        const double lu = link * V.inv_h;                       // linking length in fine units
+        const double lu = link / V.h;                           // linking length in fine units
         const float lo_thr = (float)(lu * lu * (1.0 - kBand));
         const float hi_thr = (float)(lu * lu * (1.0 + kBand));
         const float cull = (float)(lu * (1.0 + kBand)) * (1.0f + 1.0f / 512.0f);

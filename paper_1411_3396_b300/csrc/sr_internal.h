@@ -27,7 +27,7 @@ struct VolDev {
     double h;            // fine cell side, L / M
     double inv_h;        // 1/h, used instead of a division when h is a power of two
     int h_pow2;          // 1 if h is an exact power of two (then x * inv_h == x / h)
-    int pad1;
+    int inv_h_exp;       // s with inv_h = 2^s (when h_pow2)
     long long part_start;  // first caller row of the volume
     long long part_end;
     int n_c;             // cells per axis

@@ -1,4 +1,6 @@
 """sr_bin on the GPU is bit-exact against the oracle's binning spec."""
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -110,3 +112,70 @@ def test_bin_partial_fill_and_rebin():
         plan.bin(torch.from_numpy(pos).cuda())
         torch.cuda.synchronize()
         _compare(plan, [(pos, L)])
+
+
+@pytest.mark.parametrize("sub_bits,chunk", [(6, 32), (3, 64), (6, 64)])
+def test_bin_power_of_two_side_with_sub_cells(sub_bits, chunk):
+    # box 32, 8 cells: h = 4 / 2^b is a power of two (the integer path of the
+    # binning kernels), sub-cells put anchors and slots in different fine cells
+    w = wc.make_workload(wc.small_variant("clustered256"))
+    plan = _run_bin(w["volumes"], w["params"], sub_bits=sub_bits, n_cells=[8], chunk_size=chunk)
+    _compare(plan, w["volumes"])
+
+
+def _rn(value: Fraction, bits: int) -> Fraction:
+    """value rounded to `bits` significant bits, to nearest, ties to even."""
+    if value == 0:
+        return value
+    sign = -1 if value < 0 else 1
+    a = abs(value)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    scale = Fraction(2) ** (bits - 1 - e)
+    m = a * scale
+    fl = m.numerator // m.denominator
+    rem = m - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
+        fl += 1
+    return sign * Fraction(fl) / scale
+
+
+def test_bin_offsets_round_twice_like_the_spec():
+    # the offset is binary32(t - qa) with the subtraction in binary64; for a
+    # slot near a cell's start under a far anchor the difference needs more
+    # than 53 bits, and these pairs are built so that the binary64 rounding
+    # lands exactly on a binary32 tie (or just short of one)
+    box, b = 32.0, 6                     # 8 cells of 64 fine cells, h = 1/16
+    m24 = 10092545                       # odd: a tie rounds it up to even
+    tie = Fraction(2 * m24 + 1, 2 ** 19)  # (m24 + 1/2) 2^-18, in [38, 39)
+    eps_cases = [Fraction(1, 2 ** 51), Fraction(1, 2 ** 50), Fraction(1, 2 ** 49), Fraction(1, 2 ** 48),
+                 Fraction(3, 2 ** 49), Fraction(1, 2 ** 52)]
+    pts, expect = [], []
+    for n, eps in enumerate(eps_cases):
+        cy, cz = n % 4, n // 4            # one cell per case along y, z; x in the first cell
+        oy, oz = 64 * cy, 64 * cz        # cell origins in fine units
+        t = 40 - tie + eps               # exact in binary64: t in [1, 2), ulp 2^-52
+        assert Fraction(float(t)) == t
+        d = t - 40                       # offset of the slot against the anchor qa = 40
+        twice = _rn(_rn(d, 53), 24)
+        once = _rn(d, 24)
+        expect.append((n, twice, once))
+        # anchor (first in Morton order: its key has only x bits), then the slot
+        pts.append([40.25 / 16, (oy + 0.25) / 16, (oz + 0.25) / 16])
+        pts.append([float(t) / 16, (oy + 32.5) / 16, (oz + 0.25) / 16])
+    # the same on the y axis: the slot's z sub-cell orders it after the anchor
+    t = 40 - tie + eps_cases[0]
+    pts.append([(64 * 5 + 0.25) / 16, 40.25 / 16, (64 * 5 + 0.25) / 16])
+    pts.append([(64 * 5 + 0.25) / 16, float(t) / 16, (64 * 5 + 32.5) / 16])
+    pos = np.array(pts)
+    assert sum(1 for _, tw, on in expect if tw != on) >= 3      # real double-rounding cases
+    vols = [(pos, box)]
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), sub_bits=b, n_cells=[8], chunk_size=32)
+    _compare(plan, vols)
+    # and the offsets are the twice-rounded values
+    sp = to_np(plan.export("slot_pos"))
+    idx = to_np(plan.export("slot_idx"))
+    for n, twice, _ in expect:
+        row = int(np.nonzero(idx == 2 * n + 1)[0][0])
+        assert Fraction(float(sp.reshape(-1, 4)[row, 0])) == twice

@@ -52,6 +52,19 @@ def test_clustered_labels_bit_exact(link, min_members, chunk):
           f"{info['links']} links, {info['band_checks']} binary64 checks")
 
 
+def test_cell_side_not_a_power_of_two():
+    # box 30: 7 cells of side 30/7, so the fine-grid side h is not a power of
+    # two and positions are scaled by a binary64 division
+    pos, _, _ = gen.nfw_clustered(12000, 30.0, 71, m_lo=40.0, m_hi=2000.0)
+    for link, mm in ((0.2, 20), (0.3, 5)):
+        lab, sizes, info = _gpu_fof([(pos, 30.0)], PARAMS, link, mm)
+        lab_o, sizes_o = ofof.fof(pos, 30.0, link, mm)
+        np.testing.assert_array_equal(lab, lab_o)
+        np.testing.assert_array_equal(sizes, sizes_o)
+        assert info["links"] == len(ofof.friend_pairs(pos, 30.0, link))
+        assert info["n_halos"] > 0
+
+
 def test_special_configurations():
     L = 20.0
     line = np.zeros((60, 3)) + 7.0
