@@ -70,29 +70,43 @@ __device__ __forceinline__ double fold(double v, double box) {
     return v;
 }
 
+constexpr int kNotPow2 = 1 << 30;      // inv_s when n / L is not a power of two
+
 // Base cell and binary32 fractions of one particle (the cell and the
 // fraction are formed in binary64; the weights that use the fraction run
-// in binary32).
+// in binary32).  When inv_d = n / L = 2^inv_s and x lies in [0, L), the same
+// values come from the bit pattern (exact scaling, floor and the exact
+// fraction rounded once to binary32); otherwise, and for u < 1, binary64
+// arithmetic.
 __device__ __forceinline__ void cic_cell(const double* __restrict__ pos, long long i, double box, double inv_d,
-                                         int n, int (&c)[3], float (&f)[3]) {
+                                         int inv_s, int n, int (&c)[3], float (&f)[3]) {
+    const unsigned long long ubox = (unsigned long long)__double_as_longlong(box);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double u = fold(pos[3 * i + a], box) * inv_d;
-        const double fl = floor(u);
-        f[a] = (float)(u - fl);
-        int ci = (int)fl;
-        c[a] = ci >= n ? ci - n : ci;
+        const double x = pos[3 * i + a];
+        int q, F;
+        unsigned long long mant;
+        if (inv_s != kNotPow2 && sr::fine_axis_bits(x, ubox, inv_s, q, mant, F) && F >= 0) {
+            f[a] = sr::fraction_bits(mant, F);
+            c[a] = q >= n ? q - n : q;
+        } else {
+            const double u = fold(x, box) * inv_d;
+            const double fl = floor(u);
+            f[a] = (float)(u - fl);
+            const int ci = (int)fl;
+            c[a] = ci >= n ? ci - n : ci;
+        }
     }
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_cic_deposit(const double* __restrict__ pos, long long np, double box, double inv_d, int n, float scale,
-              unsigned long long* __restrict__ grid) {
+k_cic_deposit(const double* __restrict__ pos, long long np, double box, double inv_d, int inv_s, int n,
+              float scale, unsigned long long* __restrict__ grid) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     int c[3];
     float f[3];
-    cic_cell(pos, i, box, inv_d, n, c, f);
+    cic_cell(pos, i, box, inv_d, inv_s, n, c, f);
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
         const float wx = dx ? f[0] : 1.f - f[0];
@@ -423,13 +437,13 @@ __global__ void k_pm_extract(const float2* __restrict__ w, long long n3, int ca,
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_cic_interp(const double* __restrict__ pos, long long np, double box, double inv_d, int n,
+k_cic_interp(const double* __restrict__ pos, long long np, double box, double inv_d, int inv_s, int n,
              const float4* __restrict__ accg, float4* __restrict__ acc, int accumulate) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     int c[3];
     float f[3];
-    cic_cell(pos, i, box, inv_d, n, c, f);
+    cic_cell(pos, i, box, inv_d, inv_s, n, c, f);
     float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
@@ -486,6 +500,15 @@ struct sr_pm {
     bool transformed = false;
     bool accel_valid = false;
 };
+
+namespace {
+// s with n / L = 2^s, or kNotPow2 (the CIC kernels' integer path needs it).
+int mesh_exp(const sr_pm* pm) {
+    int ex = 0;
+    const double m = std::frexp(pm->n / pm->box, &ex);
+    return m == 0.5 ? ex - 1 : kNotPow2;
+}
+}  // namespace
 
 namespace {
 
@@ -712,8 +735,8 @@ int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double scale = std::ldexp(1.0, pm->fixed_shift);
     SR_CUDA_CHECK(cudaMemsetAsync(pm->fx, 0, sizeof(unsigned long long) * (size_t)pm->n3, st));
-    k_cic_deposit<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box, pm->n,
-                                                              (float)scale, pm->fx);
+    k_cic_deposit<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box,
+                                                              mesh_exp(pm), pm->n, (float)scale, pm->fx);
     SR_LAUNCH_CHECK("k_cic_deposit");
     pm->last_np = n;
     pm->deposited = true;
@@ -781,8 +804,9 @@ int sr_pm_force(sr_pm* pm, const double* pos, int64_t n, float* acc, int accumul
         SR_LAUNCH_CHECK("k_pm_extract");
         pm->accel_valid = true;
     }
-    k_cic_interp<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box, pm->n,
-                                                             pm->accg, reinterpret_cast<float4*>(acc), accumulate);
+    k_cic_interp<<<grid_for(n, kThreads), kThreads, 0, st>>>(pos, (long long)n, pm->box, pm->n / pm->box,
+                                                             mesh_exp(pm), pm->n, pm->accg,
+                                                             reinterpret_cast<float4*>(acc), accumulate);
     SR_LAUNCH_CHECK("k_cic_interp");
     return SR_OK;
 }

@@ -13,6 +13,88 @@ namespace sr {
 
 constexpr int kMaxChunkK = 2;       // chunks hold 32 K particles, K = 1 or 2 (K per lane)
 constexpr float kPad = 1.0e30f;     // coordinate of an empty slot: never within r_c
+
+#ifdef __CUDACC__
+// Integer forms of the exact binary64 steps that place a coordinate on a
+// grid of spacing 2^-s (binning's fine grid, the PM mesh).  B300 runs
+// binary64 arithmetic at a small fraction of its integer rate, and these
+// few operations otherwise bound the kernels that use them.
+//
+// x in [0, box) (checked on its bit pattern: non-negative doubles order as
+// their bits), so t = x * 2^s is exact and floor(t) can be read off the
+// significand.  Returns false for anything else (negative or -0, >= box,
+// NaN, inf), which the caller sends through its binary64 code.  On success:
+// q = floor(t) and, when t >= 1, t = mant * 2^-F with F = 52 - E in
+// [0, 52] (F = -1 when t < 1).
+__device__ __forceinline__ bool fine_axis_bits(double x, unsigned long long ubox, int s, int& q,
+                                               unsigned long long& mant, int& F) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if (u >= ubox) return false;
+    const int e = (int)(u >> 52);                 // biased exponent (sign bit clear)
+    const int E = e - 1023 + s;                   // exponent of t
+    if (e == 0 || E < 0) {                        // zero, subnormal x, or t < 1
+        q = 0;
+        mant = 0ull;
+        F = -1;
+        return true;
+    }
+    mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    if (E > 52) return false;                     // t >= 2^53: not a grid coordinate here
+    F = 52 - E;
+    q = (int)(mant >> F);
+    return true;
+}
+
+// Round the positive integer a (< 2^63) to nb significant bits, to nearest
+// with ties to even; the result keeps a's scale.  *msb is the position of the
+// leading bit before and after (it moves up by one when the rounding carries).
+__device__ __forceinline__ unsigned long long round_bits(unsigned long long a, int nb, int* msb) {
+    const int sh = *msb - (nb - 1);
+    if (sh <= 0) return a;
+    unsigned long long m = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+        ++m;
+        if (m == (1ull << nb)) {
+            m >>= 1;
+            ++*msb;
+            return m << (sh + 1);
+        }
+    }
+    return m << sh;
+}
+
+// binary32(binary64(t - qa)) for t = mant * 2^-F (F in [30, 52]), q =
+// floor(t) and |q - qa| < 2^30: the difference held exactly as the integer
+// d = (t - qa) 2^F, rounded to 53 significant bits (the binary64 subtraction)
+// and then to 24 (the conversion), both to nearest even.
+__device__ __forceinline__ float offset_bits(unsigned long long mant, int F, int q, int qa) {
+    const unsigned long long frac = mant & ((1ull << F) - 1ull);
+    const long long d = (long long)(q - qa) * (1ll << F) + (long long)frac;
+    if (d == 0) return 0.0f;
+    const unsigned int sgn = d < 0 ? 0x80000000u : 0u;
+    unsigned long long a = d < 0 ? (unsigned long long)(-d) : (unsigned long long)d;
+    int msb = 63 - __clzll((long long)a);
+    a = round_bits(a, 53, &msb);
+    a = round_bits(a, 24, &msb);
+    const unsigned int m24 = (unsigned int)(msb >= 23 ? a >> (msb - 23) : a << (23 - msb));
+    const int ex = msb - F + 127;                 // |t - qa| in [2^-52, 2^31): a normal binary32
+    return __uint_as_float(sgn | ((unsigned int)ex << 23) | (m24 & 0x7FFFFFu));
+}
+
+// binary32 rounding (to nearest even) of the fraction t - floor(t), for
+// t = mant * 2^-F, F in [0, 52]; the binary64 subtraction is exact.
+__device__ __forceinline__ float fraction_bits(unsigned long long mant, int F) {
+    unsigned long long a = F ? (mant & ((1ull << F) - 1ull)) : 0ull;
+    if (a == 0ull) return 0.0f;
+    int msb = 63 - __clzll((long long)a);
+    a = round_bits(a, 24, &msb);
+    const unsigned int m24 = (unsigned int)(msb >= 23 ? a >> (msb - 23) : a << (23 - msb));
+    const int ex = msb - F + 127;                 // fraction in [2^-52, 1)
+    return __uint_as_float(((unsigned int)ex << 23) | (m24 & 0x7FFFFFu));
+}
+#endif  // __CUDACC__
+
 constexpr int kScanItems = 8;       // items per thread in scans / radix passes
 constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
