@@ -109,6 +109,39 @@ def kernel_source_hash(names=("force.cu", "sr_internal.h")):
     return h.hexdigest()[:12]
 
 
+BIN_BYTES_PER_PARTICLE = 44    # 24 B of binary64 position read, 16 B slot offsets + 4 B slot index written
+KICK_BYTES_PER_PARTICLE = 48   # acceleration and velocity rows read (16 + 16 B), velocity row written (16 B)
+
+
+def time_hbm_kernels(plan, x, acc, vel, n, hbm_gbs, reps=5):
+    """sr_bin and the separate sr_kick timed alone (CUDA events on the
+    current stream, after the timed step; inputs larger than L2), against
+    their algorithmic bytes and the measured HBM copy bandwidth."""
+    import torch
+    from paper_1411_3396_b300 import kick
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    plan.bin(x)
+    kick(acc, vel, 0.0)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        plan.bin(x)
+    ev[1].record()
+    ev[2].record()
+    for _ in range(reps):
+        kick(acc, vel, 0.0)                    # dt = 0: velocities unchanged
+    ev[3].record()
+    torch.cuda.synchronize()
+    out = {}
+    for name, ms, bpp in (("sr_bin", ev[0].elapsed_time(ev[1]) / reps, BIN_BYTES_PER_PARTICLE),
+                          ("sr_kick", ev[2].elapsed_time(ev[3]) / reps, KICK_BYTES_PER_PARTICLE)):
+        gbs = n * bpp / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes_per_particle": bpp, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm_gbs}
+    out["note"] = ("sr_bin includes the 5-pass radix sort and the gather of positions into slots; "
+                   "the time step fuses the kick into the force kernel")
+    return out
+
+
 def recorded_traffic(note=PROFILE_NOTE, names=("force.cu", "sr_internal.h")):
     """DRAM bytes per launch of a kernel from its committed ncu summary, or
     None if the summary is missing or was taken on a different kernel source."""
@@ -389,6 +422,7 @@ def run_ours(args, rank, world, local_rank):
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = pairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12
     traffic = recorded_traffic()
+    hbm_kernels = None if batch else time_hbm_kernels(plan, x, acc, vel, n, float(peaks.get("hbm_gbs", 6400.0)))
 
     if rank != 0:
         return
@@ -414,6 +448,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived, not measured)",
                      "flops_per_pair": FLOPS_PER_PAIR},
         "plain": plain,
+        "hbm_kernels": hbm_kernels,
         "e2e": e2e,
         "gpu_launches": int(l1 - l0),
         "clocks": clocks,
