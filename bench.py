@@ -1127,7 +1127,7 @@ def run_diff(args, rank, world, local_rank):
     pairs (the same pair sets again in the backward sweep)."""
     import torch
 
-    from paper_1411_3396_b300 import Plan, launch_count, trajectory
+    from paper_1411_3396_b300 import Plan, TrajectoryGraph, launch_count, trajectory
     from workloads import configs as wc
     from workloads import generators as gen
 
@@ -1146,13 +1146,16 @@ def run_diff(args, rank, world, local_rank):
     vd[:, :3] = torch.from_numpy(v0).to(dev).float()
     target = torch.from_numpy(xt).to(dev)
 
-    def one(xi, vi):
+    def loss_fn(xk, vk):
+        d = xk - target
+        d = d - box * torch.round(d / box)
+        return (d * d).sum()
+
+    def eager(xi, vi):
         x = xi.detach().clone().requires_grad_(True)
         v = vi.detach().clone().requires_grad_(True)
         xk, vk = trajectory(plan, x, v, steps, dt)
-        d = xk - target
-        d = d - box * torch.round(d / box)
-        loss = (d * d).sum()
+        loss = loss_fn(xk, vk)
         loss.backward()
         return loss, x.grad, v.grad
 
@@ -1174,10 +1177,28 @@ def run_diff(args, rank, world, local_rank):
     else:
         plan.bin(xd)
         plan.autotune(reps=2)
+    # eager trajectories (autograd issuing every launch from the host), then
+    # the same sweep captured once in a CUDA graph and replayed
+    for _ in range(args.warmup):
+        eager(xd, vd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        eager(xd, vd)
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / args.steps
+    if args.no_graph:
+        one = eager
+    else:
+        tg = TrajectoryGraph(plan, xd, vd, steps, dt, loss_fn)
+
+        def one(xi, vi):
+            return tg.run(xi, vi)
     for _ in range(args.warmup):
         one(xd, vd)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = launch_count()
     e0.record()
     for _ in range(args.steps):
@@ -1185,6 +1206,8 @@ def run_diff(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     l1 = launch_count()
+    if not args.no_graph:
+        l1 = l0 + tg.kernels * args.steps         # replays launch the captured kernels
     ms = e0.elapsed_time(e1) / args.steps
     total_pairs = 2 * pairs
     # kernel roofline on the initial configuration: force + VJP
@@ -1237,6 +1260,7 @@ def run_diff(args, rank, world, local_rank):
                    "r_c": cfg["rc"], "eps": cfg["eps"], "sigma": cfg["sigma"],
                    "pairs_forward": pairs, "pairs_per_step": total_pairs,
                    "trajectories_per_s": 1e3 / ms, "loss": float(loss.item()),
+                   "graph": not args.no_graph, "eager_ms_per_step": eager_ms,
                    "parallelism": "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
@@ -1270,6 +1294,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="diff64: time eager trajectories only")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variant", type=int, default=-1, help="force a pair-kernel variant (skips autotuning)")

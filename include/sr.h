@@ -358,7 +358,10 @@ int sr_graph_launch(sr_plan* plan, void* stream);
 const char* sr_last_error(void);
 
 /* sr_launch_count -- number of kernels this library has launched so far
- * (process-wide, all threads). */
+ * (process-wide, all threads).  The kernels of a graph made by
+ * sr_graph_capture count at each sr_graph_launch, not at the capture.
+ * Kernels captured by the caller's own stream capture count once, when
+ * they are captured. */
 int64_t sr_launch_count(void);
 
 #ifdef __cplusplus

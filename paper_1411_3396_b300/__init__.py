@@ -15,6 +15,6 @@ from .centers import Centers  # noqa: F401
 from .pm import PM  # noqa: F401
 from .fof import FOF  # noqa: F401
 from .decomp import Slabs, slab_bounds  # noqa: F401
-from .autograd import trajectory  # noqa: F401
+from .autograd import TrajectoryGraph, trajectory  # noqa: F401
 from ._lib import SrError  # noqa: F401
 from .build import LIB, build  # noqa: F401

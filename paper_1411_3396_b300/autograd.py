@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import torch
 
-from .api import Plan, kick
+from .api import Plan, kick, launch_count
 
 
 class _Trajectory(torch.autograd.Function):
@@ -65,3 +65,50 @@ class _Trajectory(torch.autograd.Function):
 def trajectory(plan: Plan, x0: torch.Tensor, v0: torch.Tensor, steps: int, dt: float):
     """(x_K, v_K) after ``steps`` kick-drift substeps; differentiable in x0, v0."""
     return _Trajectory.apply(x0, v0, plan, int(steps), float(dt))
+
+
+class TrajectoryGraph:
+    """A trajectory, a scalar loss on its end state and the gradient sweep,
+    captured once in a CUDA graph and replayed.
+
+    ``loss_fn(x_K, v_K)`` returns a scalar tensor.  Each ``run(x0, v0)``
+    copies the inputs into the graph's static buffers and replays the
+    captured kernels (the same kernels in the same order as the eager
+    ``trajectory`` plus ``torch.autograd.grad``, so the results are
+    bit-identical to it) without the per-launch host work; it returns
+    static tensors (loss, dloss/dx0 (n, 3) binary64, dloss/dv0 (n, 4)
+    binary32) that the next ``run`` overwrites.  The library calls on the
+    path are capture-safe: they neither allocate nor synchronise.
+    """
+
+    def __init__(self, plan: Plan, x0: torch.Tensor, v0: torch.Tensor, steps: int, dt: float, loss_fn,
+                 warmup: int = 2):
+        self.plan, self.steps, self.dt, self.loss_fn = plan, int(steps), float(dt), loss_fn
+        self.x = x0.detach().clone().requires_grad_(True)
+        self.v = v0.detach().clone().requires_grad_(True)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(max(1, int(warmup))):
+                self._sweep()
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        k0 = launch_count()
+        with torch.cuda.graph(self.graph):
+            self.loss, self.gx, self.gv = self._sweep()
+        self.kernels = launch_count() - k0          # library kernels in one replay
+
+    def _sweep(self):
+        xk, vk = trajectory(self.plan, self.x, self.v, self.steps, self.dt)
+        loss = self.loss_fn(xk, vk)
+        gx, gv = torch.autograd.grad(loss, (self.x, self.v))
+        return loss.detach(), gx, gv
+
+    def run(self, x0: torch.Tensor | None = None, v0: torch.Tensor | None = None):
+        with torch.no_grad():
+            if x0 is not None:
+                self.x.copy_(x0)
+            if v0 is not None:
+                self.v.copy_(v0)
+        self.graph.replay()
+        return self.loss, self.gx, self.gv

@@ -263,7 +263,11 @@ int cuda_fail(cudaError_t e, const char* what) {
     return SR_ERR_CUDA;
 }
 
-void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+thread_local long long t_launches = 0;     // this thread's launches (a capture's own count)
+void note_launch(int k) {
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+    t_launches += k;
+}
 
 }  // namespace sr
 
@@ -540,8 +544,13 @@ int sr_graph_capture(sr_plan* p, const double* pos, float* vel, float* acc, floa
         return set_error(SR_ERR_CAPACITY, "a batch plan bins exactly the sum of its volume counts");
     cudaStream_t st = as_stream(stream);
     SR_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const long long t0 = t_launches;
     int rc = launch_bin(p, pos, n, st);
     if (!rc) rc = launch_force(p, acc, nullptr, nullptr, st, vel, dt);      // kick fused into the epilogue
+    const long long captured = t_launches - t0;
+    // captured kernels run at each sr_graph_launch, not now
+    g_launches.fetch_sub(captured, std::memory_order_relaxed);
+    t_launches = t0;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (rc) {
@@ -555,6 +564,7 @@ int sr_graph_capture(sr_plan* p, const double* pos, float* vel, float* acc, floa
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     p->graph_exec = ex;
+    p->graph_kernels = captured;
     p->n_binned = n;
     p->binned = true;
     return SR_OK;
@@ -564,6 +574,7 @@ int sr_graph_launch(sr_plan* p, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->graph_exec) return set_error(SR_ERR_STATE, "no captured graph");
     SR_CUDA_CHECK(cudaGraphLaunch(p->graph_exec, as_stream(stream)));
+    note_launch((int)p->graph_kernels);
     return SR_OK;
 }
 

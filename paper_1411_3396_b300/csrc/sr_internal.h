@@ -196,6 +196,7 @@ struct sr_plan {
 
     // captured whole-step graph (sr_graph_capture)
     cudaGraphExec_t graph_exec = nullptr;
+    long long graph_kernels = 0;       // library kernels in the captured graph
 
     // staging for sr_step_host
     double* h_pos_dev = nullptr;

@@ -55,13 +55,21 @@ def test_graph_replay_equals_eager():
     xg = x.clone()
     vg = v0.clone()
     ag = torch.zeros_like(vg)
+    from paper_1411_3396_b300 import launch_count
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
+        k0 = launch_count()
         plan.graph_capture(xg, vg, ag, prm["dt"])
+        assert launch_count() == k0                          # captured kernels count when replayed
         assert float(ag.abs().sum().item()) == 0.0          # capture ran nothing
+        k1 = launch_count()
+        plan.graph_launch()
+        per_replay = launch_count() - k1
+        assert per_replay >= 8                               # binning passes + the force kernel
         for _ in range(3):
             vg.copy_(v0)
             plan.graph_launch()
+        assert launch_count() - k1 == 4 * per_replay
     torch.cuda.synchronize()
     assert to_np(ag).tobytes() == to_np(ae).tobytes()
     assert to_np(vg).tobytes() == to_np(ve).tobytes()

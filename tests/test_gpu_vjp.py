@@ -137,3 +137,42 @@ def test_trajectory_full_size_64cubed():
         norm = np.linalg.norm(g - r) / np.linalg.norm(r)
         assert np.median(rel) <= 1e-5 and norm <= 1e-4 and rel.max() <= 1e-3, \
             (np.median(rel), norm, rel.max())
+
+
+def test_trajectory_graph_is_bit_identical_to_eager():
+    # the captured forward + loss + gradient sweep replays the eager kernels
+    from paper_1411_3396_b300 import TrajectoryGraph, trajectory
+    w = wc.make_workload(wc.small_variant("diff64"))
+    (pos, box), = w["volumes"]
+    prm = w["params"]
+    plan = make_plan(w["volumes"], prm)
+    n = len(pos)
+    rng = np.random.default_rng(8)
+    target = torch.from_numpy(np.mod(pos + rng.normal(0, 0.2, pos.shape), box)).cuda()
+
+    def loss_fn(xk, vk):
+        d = xk - target
+        d = d - box * torch.round(d / box)
+        return (d * d).sum() + 0.5 * (vk[:, :3].double() ** 2).sum()
+
+    def eager(x0, v0):
+        x = x0.clone().requires_grad_(True)
+        v = v0.clone().requires_grad_(True)
+        xk, vk = trajectory(plan, x, v, 4, prm["dt"])
+        loss = loss_fn(xk, vk)
+        gx, gv = torch.autograd.grad(loss, (x, v))
+        return loss.detach(), gx, gv
+
+    x0 = torch.from_numpy(pos).cuda()
+    v0 = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    v0[:, :3] = torch.from_numpy(rng.normal(0, 0.3, (n, 3))).float().cuda()
+    g = TrajectoryGraph(plan, x0, v0, 4, prm["dt"], loss_fn)
+    for trial in range(2):
+        if trial:
+            x0 = torch.from_numpy(np.mod(pos + rng.normal(0, 0.05, pos.shape), box)).cuda()
+            v0 = v0 * 0.5
+        ref = eager(x0, v0)
+        got = g.run(x0, v0)
+        torch.cuda.synchronize()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b)
