@@ -93,6 +93,37 @@ def cpu_oracle_sample(pos, box, prm, n_rows, seed, cores, reps=1):
 # helpers
 # ---------------------------------------------------------------------------
 
+# Metric names: each workload's own arm and its oracle reference arm print
+# the same metric, so the two lines compare directly.
+METRICS = {
+    "force": "short-range pair interactions/sec (FP32) and % of B300 FP32 peak vs plain kernel",
+    "centers256": "halo center finding: unordered member pair potentials/sec (FP32, most-bound particle)",
+    "pm256": "long-range PM step (CIC deposit, FFT, P(k), filtered PM accelerations): particles/sec",
+    "fof256": "friends-of-friends halo finding (b=0.168, >=40 particles) incl. binning: particles/sec",
+    "step256": "whole force-split time step (binning, short-range pairs, PM with P(k), kick): particles/sec",
+    "diff64": "short-range pair interactions/sec (FP32), forward + VJP of a differentiable trajectory",
+}
+
+
+def host_cpu_model():
+    """Model name of the host CPU (the oracle's timing context), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def emit(line):
+    """Print the bench line; a CPU baseline also names the host CPU model."""
+    if isinstance(line.get("cpu_baseline"), dict):
+        line["cpu_baseline"].setdefault("cpu_model", host_cpu_model())
+    print(json.dumps(line), flush=True)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -256,6 +287,59 @@ def make_inputs(name, n_particles=0, world=1, rank=0):
 # arms
 # ---------------------------------------------------------------------------
 
+def cpu_diff_sample(n_req, reps, warmup=0):
+    """The oracle's own differentiable trajectory on the diff64 workload
+    resized to a bounded sample (16^3 particles, or n_req if fewer): FP64
+    kick-drift substeps and the hand-written reverse sweep, each repetition
+    timed; pairs counted as in the GPU arm (forward pairs twice).  Returns
+    (pairs/s per timed repetition, n, substeps)."""
+    from scipy.spatial import cKDTree
+
+    from oracle import fit as ofit
+    from oracle import integrate as oint
+    from workloads import configs as wc
+    from workloads import generators as gen
+    cfg = wc.resized("diff64", min(n_req or 16 ** 3, 16 ** 3))
+    box, n_side, steps, dt = cfg["box"], cfg["n_side"], cfg["steps"], cfg["dt"]
+    x0, psi = gen.zeldovich(n_side, box, cfg.get("rms", 0.5), cfg["seed"])
+    xt, _ = gen.zeldovich(n_side, box, cfg.get("rms", 0.5), cfg["seed"] + 1)
+    v0 = 0.1 * psi
+    c = ofit.fit_poly(cfg["rc"], cfg["sigma"], cfg["eps"])
+    xs, _ = oint.trajectory(x0, v0, box, cfg["rc"], cfg["eps"], c, dt, steps)
+    pairs = 0
+    for x in xs[:-1]:
+        pairs += 2 * len(cKDTree(x, boxsize=box).query_pairs(cfg["rc"], output_type="ndarray"))   # ordered
+    rates = []
+    for k in range(warmup + reps):
+        t0 = time.perf_counter()
+        oint.loss_and_grad(x0, v0, xt, box, cfg["rc"], cfg["eps"], c, dt, steps)
+        el = time.perf_counter() - t0
+        if k >= warmup:
+            rates.append(2 * pairs / el)
+    return rates, len(x0), steps
+
+
+def diff_sample_note(n, steps):
+    return (f"the diff64 workload resized to {n} particles: FP64 trajectory of {steps} substeps and its "
+            "reverse sweep (k-d tree pair sums, NumPy, one thread)")
+
+
+def run_reference_diff(args, rank, world):
+    rates, n, steps = cpu_diff_sample(args.n_particles, args.steps, args.warmup)
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRICS["diff64"],
+        "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "diff64", "n_particles": n, "substeps": steps},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                         "sample": diff_sample_note(n, steps)},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    emit(line)
+
+
 def run_reference(args, rank, world):
     cfg, vols, vel, prm = make_inputs(args.workload, args.n_particles)
     if rank != 0:
@@ -267,7 +351,7 @@ def run_reference(args, rank, world):
     per = per[args.warmup:]
     value = float(np.mean(per))
     line = {
-        "impl": "reference", "metric": "short-range pair interactions/sec (FP32 path; oracle FP64)",
+        "impl": "reference", "metric": METRICS["force"],
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -278,7 +362,7 @@ def run_reference(args, rank, world):
                                    "(FP64 k-d tree row sums; tree build untimed)"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -427,7 +511,7 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     line = {
-        "metric": "short-range pair interactions/sec (FP32) and % of B300 FP32 peak vs plain kernel",
+        "metric": METRICS["force"],
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
@@ -454,7 +538,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     plan.close()
 
 
@@ -611,7 +695,7 @@ def run_centers(args, rank, world, local_rank):
         ctr.close()
         return
     line = {
-        "metric": "halo center finding: unordered member pair potentials/sec (FP32, most-bound particle)",
+        "metric": METRICS["centers256"],
         "value": pairs_all / (ms_max * 1e-3), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -633,7 +717,7 @@ def run_centers(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     ctr.close()
 
 
@@ -777,7 +861,7 @@ def run_pm(args, rank, world, local_rank):
         pm.close()
         return
     line = {
-        "metric": "long-range PM step (CIC deposit, FFT, P(k), filtered PM accelerations): particles/sec",
+        "metric": METRICS["pm256"],
         "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -796,7 +880,7 @@ def run_pm(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     pm.close()
 
 
@@ -923,7 +1007,7 @@ def run_fof(args, rank, world, local_rank):
     if rank != 0:
         return
     line = {
-        "metric": "friends-of-friends halo finding (b=0.168, >=40 particles) incl. binning: particles/sec",
+        "metric": METRICS["fof256"],
         "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -945,7 +1029,7 @@ def run_fof(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def run_step(args, rank, world, local_rank):
@@ -1032,7 +1116,7 @@ def run_step(args, rank, world, local_rank):
     if rank != 0:
         return
     line = {
-        "metric": "whole force-split time step (binning, short-range pairs, PM with P(k), kick): particles/sec",
+        "metric": METRICS["step256"],
         "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -1048,7 +1132,7 @@ def run_step(args, rank, world, local_rank):
         "clocks": clocks,
         "cpu_baseline": None,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def run_reference_other(args, rank, world):
@@ -1080,7 +1164,7 @@ def run_reference_other(args, rank, world):
         per.append(rate)
     value = float(np.mean(per[args.warmup:]))
     line = {
-        "impl": "reference", "metric": f"{args.workload} step (oracle FP64): particles/sec",
+        "impl": "reference", "metric": METRICS[args.workload],
         "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -1090,7 +1174,7 @@ def run_reference_other(args, rank, world):
                                    f"{sample_n} particles"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def run_reference_centers(args, rank, world):
@@ -1104,7 +1188,7 @@ def run_reference_centers(args, rank, world):
     value = float(np.mean(per[args.warmup:]))
     line = {
         "impl": "reference",
-        "metric": "halo center finding: unordered member pair potentials/sec (FP32 path; oracle FP64)",
+        "metric": METRICS["centers256"],
         "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -1114,7 +1198,7 @@ def run_reference_centers(args, rank, world):
                          "sample": "per step, a seeded sample of whole halos (FP64 NumPy blocked pair sums)"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 VJP_FLOPS_PER_PAIR = 55   # d, s', r^2, r^3, q and q' (Horner), f, f', g_j - g_i, d.dg, w, two FMA per component
@@ -1251,8 +1335,13 @@ def run_diff(args, rank, world, local_rank):
     e2e_s = float(np.median(ts))
     if rank != 0:
         return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rates, n_s, st_s = cpu_diff_sample(0, 2)
+        cpu = {"value": float(np.mean(rates)), "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": diff_sample_note(n_s, st_s)}
     line = {
-        "metric": "short-range pair interactions/sec (FP32), forward + VJP of a differentiable trajectory",
+        "metric": METRICS["diff64"],
         "value": total_pairs / (ms * 1e-3), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -1269,9 +1358,9 @@ def run_diff(args, rank, world, local_rank):
         "e2e": {"value": total_pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(n * (24 + 16)),
                 "d2h_bytes_per_step": int(n * (24 + 16)), "ms_per_step": e2e_s * 1e3},
         "gpu_launches": int(l1 - l0),
-        "cpu_baseline": None,
+        "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     plan.close()
 
 
@@ -1312,6 +1401,8 @@ def main():
                 run_reference_centers(args, rank, world)
             elif args.workload in ("pm256", "fof256", "step256"):
                 run_reference_other(args, rank, world)
+            elif args.workload == "diff64":
+                run_reference_diff(args, rank, world)
             else:
                 run_reference(args, rank, world)
         return
