@@ -229,7 +229,11 @@ int sr_force_plain(sr_plan* plan, float* acc, void* stream);
  *   d = x_j - x_i, f'(s) = -3/2 (s+eps^2)^(-5/2) - p'(s),
  * for the positions of the last sr_bin.  g_acc: device float4 rows (the
  * cotangent on acc); g_pos: device float4 rows, overwritten (accumulate = 0)
- * or added to (accumulate = 1).
+ * or added to (accumulate = 1).  Plans with 32-particle chunks run the
+ * packed two-wide binary32 pair loop (each term the same binary32
+ * operations as the scalar loop; even and odd neighbours summed separately
+ * over batches of 64 before the compensated update); 64-particle chunks the
+ * scalar loop.  Deterministic.
  * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null pointers).
  */
 int sr_force_vjp(sr_plan* plan, const float* g_acc, float* g_pos, float g_scale,

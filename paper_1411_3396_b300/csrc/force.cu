@@ -38,6 +38,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kRing = 128;        // per-warp ring of staged neighbours (packed batches take 64)
+constexpr int kVjpMinBlocks = 1;   // VJP kernel: 256-thread blocks, at least this many per SM
+constexpr int vjp_flags(int k) { return k == 1 ? 2 : 0; }   // packed loop for 32-particle chunks
 
 enum Mode { kForce = 0, kForceCount = 1, kVjp = 2 };
 
@@ -273,6 +275,11 @@ __device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
     f2 r;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -286,16 +293,62 @@ __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
 
 struct PConsts {
     f2 e2, n0, n1, n2, n3, n4, n5;
+    f2 d0, d1, d2, d3, d4;             // -q' coefficients (VJP only)
     float rc2;
 };
 
+template <bool VJP>
 __device__ __forceinline__ PConsts pack_consts(const Consts& K) {
     PConsts P;
     P.e2 = f2_pack(K.eps2, K.eps2);
     P.n0 = f2_pack(K.n0, K.n0); P.n1 = f2_pack(K.n1, K.n1); P.n2 = f2_pack(K.n2, K.n2);
     P.n3 = f2_pack(K.n3, K.n3); P.n4 = f2_pack(K.n4, K.n4); P.n5 = f2_pack(K.n5, K.n5);
+    if (VJP) {
+        P.d0 = f2_pack(K.d0, K.d0); P.d1 = f2_pack(K.d1, K.d1); P.d2 = f2_pack(K.d2, K.d2);
+        P.d3 = f2_pack(K.d3, K.d3); P.d4 = f2_pack(K.d4, K.d4);
+    }
     P.rc2 = K.rc2;
     return P;
+}
+
+// Two ring entries against one particle for the VJP: on each half the same
+// binary32 operations, in the same order, as pair_vjp.  Out-of-range pairs
+// select f = w = 0 (fma(0, finite, p) = p exactly).
+__device__ __forceinline__ void pair_vjp2(f2 X, f2 Y, f2 Z, f2 GJX, f2 GJY, f2 GJZ, f2 XI, f2 YI, f2 ZI,
+                                          f2 GXI, f2 GYI, f2 GZI, const PConsts& P, f2& PX, f2& PY, f2& PZ) {
+    const f2 DX = f2_sub(X, XI), DY = f2_sub(Y, YI), DZ = f2_sub(Z, ZI);
+    f2 S = f2_fma(DX, DX, P.e2);
+    S = f2_fma(DY, DY, S);
+    S = f2_fma(DZ, DZ, S);
+    float s0, s1;
+    f2_unpack(S, s0, s1);
+    const f2 R = f2_pack(rsqrt_mufu(s0), rsqrt_mufu(s1));
+    const f2 R2 = f2_mul(R, R);
+    const f2 R3 = f2_mul(R2, R);
+    f2 H = f2_fma(P.n5, S, P.n4);
+    H = f2_fma(H, S, P.n3);
+    H = f2_fma(H, S, P.n2);
+    H = f2_fma(H, S, P.n1);
+    H = f2_fma(H, S, P.n0);
+    const f2 F = f2_add(R3, H);                                      // f_u
+    f2 ND = f2_fma(P.d4, S, P.d3);
+    ND = f2_fma(ND, S, P.d2);
+    ND = f2_fma(ND, S, P.d1);
+    ND = f2_fma(ND, S, P.d0);
+    const f2 M15 = f2_mul(f2_pack(-1.5f, -1.5f), R2);
+    const f2 FP = f2_fma(M15, R3, ND);                               // f_u'
+    const f2 EX = f2_sub(GJX, GXI), EY = f2_sub(GJY, GYI), EZ = f2_sub(GJZ, GZI);
+    const f2 DOT = f2_fma(DZ, EZ, f2_fma(DY, EY, f2_mul(DX, EX)));
+    const f2 W = f2_mul(f2_mul(f2_pack(2.0f, 2.0f), FP), DOT);
+    const bool in0 = s0 < P.rc2, in1 = s1 < P.rc2;
+    float f0, f1, w0, w1;
+    f2_unpack(F, f0, f1);
+    f2_unpack(W, w0, w1);
+    const f2 Fm = f2_pack(in0 ? f0 : 0.f, in1 ? f1 : 0.f);
+    const f2 Wm = f2_pack(in0 ? w0 : 0.f, in1 ? w1 : 0.f);
+    PX = f2_fma(Wm, DX, f2_fma(Fm, EX, PX));
+    PY = f2_fma(Wm, DY, f2_fma(Fm, EY, PY));
+    PZ = f2_fma(Wm, DZ, f2_fma(Fm, EZ, PZ));
 }
 
 // Two ring entries against one particle; the same binary32 operations as
@@ -344,8 +397,8 @@ struct WarpState {
 // ring_put); its partial sums split even / odd entries like bit 0, over
 // batches of 64 neighbours (one Kahan update per 64; 2% faster than 32).
 template <int MODE, int K, int FLAGS>
-__device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, int base, int cnt,
-                                                 WarpState<MODE, K>& w, const PConsts& P) {
+__device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, float4* __restrict__ gring, int base,
+                                                 int cnt, WarpState<MODE, K>& w, const PConsts& P) {
     constexpr bool CNT = MODE == kForceCount;
     const ulonglong2* A = reinterpret_cast<const ulonglong2*>(ring);
     const f2* B = reinterpret_cast<const f2*>(ring + kRing / 2);
@@ -357,6 +410,13 @@ __device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, int 
             Af[(p >> 1) * 4 + (p & 1)] = kPad;
             Af[(p >> 1) * 4 + 2 + (p & 1)] = kPad;
             Bf[(p >> 1) * 2 + (p & 1)] = kPad;
+            if (MODE == kVjp) {                      // a finite cotangent: the pad's terms are selected away
+                float* Gf = reinterpret_cast<float*>(gring);
+                float* Hf = reinterpret_cast<float*>(gring + kRing / 2);
+                Gf[(p >> 1) * 4 + (p & 1)] = 0.f;
+                Gf[(p >> 1) * 4 + 2 + (p & 1)] = 0.f;
+                Hf[(p >> 1) * 2 + (p & 1)] = 0.f;
+            }
         }
         __syncwarp();
     }
@@ -370,7 +430,26 @@ __device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, int 
         ZI[k] = f2_pack(w.z[k], w.z[k]);
         PX[k] = PY[k] = PZ[k] = 0ull;                // (+0, +0)
     }
-    if (npairs == 32) {
+    if (MODE == kVjp) {
+        const ulonglong2* G = reinterpret_cast<const ulonglong2*>(gring);
+        const f2* Hz = reinterpret_cast<const f2*>(gring + kRing / 2);
+        f2 GXI[K], GYI[K], GZI[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            GXI[k] = f2_pack(w.gx[k], w.gx[k]);
+            GYI[k] = f2_pack(w.gy[k], w.gy[k]);
+            GZI[k] = f2_pack(w.gz[k], w.gz[k]);
+        }
+#pragma unroll 4
+        for (int m = 0; m < npairs; ++m) {
+            const ulonglong2 a = A[m0 + m], g = G[m0 + m];
+            const f2 z = B[m0 + m], gz = Hz[m0 + m];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                pair_vjp2(a.x, a.y, z, g.x, g.y, gz, XI[k], YI[k], ZI[k], GXI[k], GYI[k], GZI[k], P, PX[k], PY[k],
+                          PZ[k]);
+        }
+    } else if (npairs == 32) {
 #pragma unroll
         for (int m = 0; m < 32; ++m) {
             const ulonglong2 a = A[m0 + m];
@@ -498,7 +577,7 @@ __device__ __forceinline__ void run_batch(const float4* __restrict__ rp, const f
 template <int MODE, int K, int WARPS, int MINB, int FLAGS, bool SINGLE>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const VolDev v0) {
     constexpr int C = 32 * K;
-    constexpr bool PACKED = (FLAGS & 2) && MODE != kVjp;
+    constexpr bool PACKED = (FLAGS & 2) != 0;
     __shared__ float4 ring_p[WARPS][kRing];
     __shared__ float4 ring_g[MODE == kVjp ? WARPS : 1][kRing];
     const int warp = threadIdx.x >> 5;
@@ -516,7 +595,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
         const Item it = load_item(a, I);
         const VolDev& V = SINGLE ? v0 : a.vols[it.vol];
         const Consts KC = load_consts(V, MODE == kVjp);
-        const PConsts PK = PACKED ? pack_consts(KC) : PConsts{};
+        const PConsts PK = PACKED ? pack_consts<MODE == kVjp>(KC) : PConsts{};
         WarpState<MODE, K> w;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -557,13 +636,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
                     } else {
                         rp[slot] = make_float4(xj, yj, zj, 0.f);
                     }
-                    if (MODE == kVjp) rg[slot] = gjs[k];
+                    if (MODE == kVjp) {
+                        if (PACKED) {                        // the same pair interleaving as positions
+                            float* Gf = reinterpret_cast<float*>(rg);
+                            float* Hf = reinterpret_cast<float*>(rg + kRing / 2);
+                            Gf[(slot >> 1) * 4 + (slot & 1)] = gjs[k].x;
+                            Gf[(slot >> 1) * 4 + 2 + (slot & 1)] = gjs[k].y;
+                            Hf[(slot >> 1) * 2 + (slot & 1)] = gjs[k].z;
+                        } else {
+                            rg[slot] = gjs[k];
+                        }
+                    }
                 }
                 w.wr += __popc(m);
                 __syncwarp();
                 if (w.wr - w.rd >= (PACKED ? 64 : 32)) {
                     const int base = w.rd & (kRing - 1);
-                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, base, 64, w, PK);
+                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, rg, base, 64, w, PK);
                     else run_batch<MODE, K, FLAGS>(rp + base, rg + base, 32, w, KC);
                     w.rd += PACKED ? 64 : 32;
                     __syncwarp();
@@ -572,7 +661,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
         });
         if (w.wr > w.rd) {
             const int base = w.rd & (kRing - 1);
-            if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, base, w.wr - w.rd, w, PK);
+            if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, rg, base, w.wr - w.rd, w, PK);
             else run_batch<MODE, K, FLAGS>(rp + base, rg + base, w.wr - w.rd, w, KC);
             __syncwarp();
         }
@@ -724,7 +813,7 @@ int occupancy_k(sr_plan* p) {
     if constexpr (K == 1 || I < 4) v[I] = occ<kForce, K, W, B, F, SINGLE>(p); else v[I] = 0;
     SR_FORCE_VARIANTS(SR_OCC)
 #undef SR_OCC
-    const int c = occ<kForceCount, K, 8, 1, 0, SINGLE>(p), g = occ<kVjp, K, 8, 1, 0, SINGLE>(p);
+    const int c = occ<kForceCount, K, 8, 1, 0, SINGLE>(p), g = occ<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), SINGLE>(p);
     for (int i = 0; i < kVariants; ++i)
         if (v[i] < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");   // 0 = not built for this K
     if (c < 0 || g < 0) return set_error(SR_ERR_CUDA, "occupancy query failed");
@@ -752,6 +841,15 @@ void launch_mode(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
     const VolDev& v0 = p->vols_h[0];
     if (p->n_vol == 1) k_pairs<MODE, K, 8, 1, 0, true><<<blocks, kThreads, 0, st>>>(a, v0);
     else k_pairs<MODE, K, 8, 1, 0, false><<<blocks, kThreads, 0, st>>>(a, v0);
+}
+
+// The VJP kernel: packed f32x2 pair loop for 32-particle chunks, the scalar
+// loop for 64-particle chunks.
+template <int K>
+void launch_vjp(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
+    const VolDev& v0 = p->vols_h[0];
+    if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), true><<<blocks, kThreads, 0, st>>>(a, v0);
+    else k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), false><<<blocks, kThreads, 0, st>>>(a, v0);
 }
 
 }  // namespace
@@ -813,8 +911,8 @@ int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int 
     a.out = g_pos;
     a.accumulate = accumulate;
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->queue, 0, sizeof(long long), st));
-    if (p->chunk_k == 2) launch_mode<kVjp, 2>(p, a, p->vjp_blocks, st);
-    else launch_mode<kVjp, 1>(p, a, p->vjp_blocks, st);
+    if (p->chunk_k == 2) launch_vjp<2>(p, a, p->vjp_blocks, st);
+    else launch_vjp<1>(p, a, p->vjp_blocks, st);
     SR_LAUNCH_CHECK("k_pairs<vjp>");
     return SR_OK;
 }
