@@ -505,7 +505,8 @@ def run_ours(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = pairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12
-    traffic = recorded_traffic()
+    # the recorded counters are for the full clustered 256^3 launch only
+    traffic = recorded_traffic() if (args.workload == "clustered256" and not args.n_particles) else None
     hbm_kernels = None if batch else time_hbm_kernels(plan, x, acc, vel, n, float(peaks.get("hbm_gbs", 6400.0)))
 
     if rank != 0:
