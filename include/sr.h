@@ -182,7 +182,7 @@ int sr_bin(sr_plan* plan, const double* pos, int64_t n, void* stream);
  *   and ADDS the total to *pair_count.
  * per_particle: device int32[n], nullable: per-particle in-range counts
  *   (written, caller order); counting mode runs a slower kernel variant.
- * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null acc).
+ * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null acc while the plan holds particles).
  */
 int sr_force(sr_plan* plan, float* acc, unsigned long long* pair_count,
              int* per_particle, void* stream);
@@ -234,7 +234,7 @@ int sr_force_plain(sr_plan* plan, float* acc, void* stream);
  * operations as the scalar loop; even and odd neighbours summed separately
  * over batches of 64 before the compensated update); 64-particle chunks the
  * scalar loop.  Deterministic.
- * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null pointers).
+ * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null pointers while the plan holds particles).
  */
 int sr_force_vjp(sr_plan* plan, const float* g_acc, float* g_pos, float g_scale,
                  int accumulate, void* stream);

@@ -65,7 +65,7 @@ int sr_fof_destroy(sr_fof* f);
  *   labels:      device int32[n] out, caller order: halo id or -1;
  *   halo_sizes:  device int32[n] out, nullable: entry h is the size of halo h
  *                (h < n_halos of sr_fof_get_info); the rest is unspecified.
- * Errors: SR_ERR_ARG (null pointers, link out of range, min_members < 1),
+ * Errors: SR_ERR_ARG (null pointers with n > 0, link out of range, min_members < 1),
  * SR_ERR_STATE (plan not binned, or binned with a different n),
  * SR_ERR_CAPACITY (n > n_max).
  */

@@ -348,20 +348,20 @@ int sr_bin(sr_plan* p, const double* pos, int64_t n, void* stream) {
 int sr_force(sr_plan* p, float* acc, unsigned long long* pair_count, int* per_particle, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->binned) return set_error(SR_ERR_STATE, "sr_force before sr_bin");
-    if (!acc) return set_error(SR_ERR_ARG, "acc is null");
+    if (!acc && p->n_binned > 0) return set_error(SR_ERR_ARG, "acc is null");
     return launch_force(p, acc, pair_count, per_particle, as_stream(stream));
 }
 
 int sr_force_kick(sr_plan* p, float* acc, float* vel, float dt, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_kick before sr_bin");
-    if (!acc || !vel) return set_error(SR_ERR_ARG, "acc or vel is null");
+    if ((!acc || !vel) && p->n_binned > 0) return set_error(SR_ERR_ARG, "acc or vel is null");
     return launch_force(p, acc, nullptr, nullptr, as_stream(stream), vel, dt);
 }
 
 int sr_leapfrog(sr_plan* p, double* pos, float* vel, float* acc, double dt, int steps, int64_t n, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
-    if (!pos || !vel || !acc) return set_error(SR_ERR_ARG, "null buffer");
+    if ((!pos || !vel || !acc) && n > 0) return set_error(SR_ERR_ARG, "null buffer");
     if (steps < 0) return set_error(SR_ERR_ARG, "steps must be >= 0");
     if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
     if (p->n_vol > 1 && n != p->capacity)
@@ -385,14 +385,14 @@ int sr_leapfrog(sr_plan* p, double* pos, float* vel, float* acc, double dt, int 
 int sr_force_plain(sr_plan* p, float* acc, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_plain before sr_bin");
-    if (!acc) return set_error(SR_ERR_ARG, "acc is null");
+    if (!acc && p->n_binned > 0) return set_error(SR_ERR_ARG, "acc is null");
     return launch_force_plain(p, acc, as_stream(stream));
 }
 
 int sr_force_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int accumulate, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->binned) return set_error(SR_ERR_STATE, "sr_force_vjp before sr_bin");
-    if (!g_acc || !g_pos) return set_error(SR_ERR_ARG, "null cotangent pointer");
+    if ((!g_acc || !g_pos) && p->n_binned > 0) return set_error(SR_ERR_ARG, "null cotangent pointer");
     return launch_vjp(p, g_acc, g_pos, g_scale, accumulate ? 1 : 0, as_stream(stream));
 }
 

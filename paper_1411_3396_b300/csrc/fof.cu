@@ -397,7 +397,8 @@ int sr_fof_destroy(sr_fof* f) {
 
 int sr_fof_run(sr_fof* f, sr_plan* p, const double* pos, int64_t n, double link, int min_members,
                int32_t* labels, int32_t* halo_sizes, void* stream) {
-    if (!f || !p || !pos || !labels) return sr::set_error(SR_ERR_ARG, "sr_fof_run: null argument");
+    if (!f || !p || ((!pos || !labels) && n > 0)) return sr::set_error(SR_ERR_ARG, "sr_fof_run: null argument");
+    if (n < 0) return sr::set_error(SR_ERR_ARG, "sr_fof_run: n must be >= 0");
     if (!(link > 0.0) || !std::isfinite(link) || min_members < 1)
         return sr::set_error(SR_ERR_ARG, "sr_fof_run: link must be > 0 and min_members >= 1");
     if (n > f->n_max) return sr::set_error(SR_ERR_CAPACITY, "sr_fof_run: n above the workspace maximum");
