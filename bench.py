@@ -1284,6 +1284,10 @@ def run_diff(args, rank, world, local_rank):
     for _ in range(args.warmup):
         one(xd, vd)
     torch.cuda.synchronize()
+    uuid = str(getattr(props, "uuid", "")) if hasattr(props, "uuid") else ""
+    sampler = ClockSampler(uuid if rank == 0 else "")
+    if rank == 0 and not args.no_clocks:
+        sampler.start()
     l0 = launch_count()
     e0.record()
     for _ in range(args.steps):
@@ -1291,6 +1295,7 @@ def run_diff(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     l1 = launch_count()
+    clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
     if not args.no_graph:
         l1 = l0 + tg.kernels * args.steps         # replays launch the captured kernels
     ms = e0.elapsed_time(e1) / args.steps
@@ -1359,6 +1364,7 @@ def run_diff(args, rank, world, local_rank):
         "e2e": {"value": total_pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": int(n * (24 + 16)),
                 "d2h_bytes_per_step": int(n * (24 + 16)), "ms_per_step": e2e_s * 1e3},
         "gpu_launches": int(l1 - l0),
+        "clocks": clocks,
         "cpu_baseline": cpu,
     }
     emit(line)
