@@ -945,7 +945,7 @@ def run_fof(args, rank, world, local_rank):
     sampler = ClockSampler(uuid if rank == 0 else "")
     if rank == 0 and not args.no_clocks:
         sampler.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         import torch.distributed as dist
@@ -1072,6 +1072,8 @@ def run_step(args, rank, world, local_rank):
         if ev is not None:
             ev[0].record()
         plan.bin(x)
+        if ev is not None:
+            ev[3].record()
         plan.force(acc)
         if ev is not None:
             ev[1].record()
@@ -1091,7 +1093,7 @@ def run_step(args, rank, world, local_rank):
     sampler = ClockSampler(uuid if rank == 0 else "")
     if rank == 0 and not args.no_clocks:
         sampler.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         import torch.distributed as dist
@@ -1109,13 +1111,46 @@ def run_step(args, rank, world, local_rank):
     clocks = sampler.stop() if (rank == 0 and not args.no_clocks) else None
     ms = t_start.elapsed_time(t_end) / args.steps
     sr_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    force_ms = float(np.mean([e[3].elapsed_time(e[1]) for e in evs]))
     lr_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     n_all, ms_max = reduce_over_ranks(n, ms, world, dev)
     plan.status()
+
+    # end to end: positions and velocities from pinned host memory, the kicked
+    # velocities back, every step
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(pos).pin_memory()
+        vel_h = vel.cpu().pin_memory()
+        out_h = torch.empty_like(vel_h).pin_memory()
+        ts = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x.copy_(pos_h, non_blocking=True)
+            vel.copy_(vel_h, non_blocking=True)
+            step()
+            out_h.copy_(vel, non_blocking=True)
+            torch.cuda.synchronize()
+            if k:
+                ts.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(ts))
+        e2e = {"value": n / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": int(n * (24 + 16)),
+               "d2h_bytes_per_step": int(n * 16), "ms_per_step": e2e_s * 1e3}
     pm.close()
     plan.close()
     if rank != 0:
         return
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = pairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, cn, el = cpu_step_sample(32 ** 3)
+        cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole oracle step on the clustered catalogue resized to {cn} particles "
+                         f"({el:.1f} s, FP64 NumPy, one thread)"}
     line = {
         "metric": METRICS["step256"],
         "value": n_all / (ms_max * 1e-3), "unit": "particles/s", "n_gpus": world, "steps": args.steps,
@@ -1127,13 +1162,38 @@ def run_step(args, rank, world, local_rank):
                    "short_range_pairs_per_s": pairs / (sr_ms * 1e-3),
                    "l2": "inputs larger than L2 (402 MB positions); no flush",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
-        "roofline": None,
-        "e2e": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_pairs<force> (the step's dominant kernel; kick applied separately after PM)",
+                     "kernel_ms": force_ms, "flops_per_pair": FLOPS_PER_PAIR,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   "(derived, not measured)"},
+        "e2e": e2e,
         "gpu_launches": int(l1 - l0),
         "clocks": clocks,
-        "cpu_baseline": None,
+        "cpu_baseline": cpu,
     }
     emit(line)
+
+
+def cpu_step_sample(sample_n):
+    """The FP64 oracle's whole force-split step (short-range accelerations
+    by k-d tree, P(k), PM accelerations) on the clustered catalogue resized
+    to sample_n particles, one thread.  Returns (particles/s, n, seconds)."""
+    from oracle import fit as ofit
+    from oracle import force as oforce
+    from oracle import pm as opm
+    from workloads import configs as wc
+    pos, box, sigma = _pm_inputs(sample_n)
+    prm = wc.CONFIGS["clustered256"]
+    c = ofit.fit_poly(prm["rc"], sigma, prm["eps"])
+    ng = int(round(len(pos) ** (1 / 3)))
+    t0 = time.perf_counter()
+    oforce.accel_kdtree(pos, box, prm["rc"], prm["eps"], c)
+    opm.power_spectrum(pos, box, ng)
+    opm.pm_accel(pos, box, ng, sigma)
+    el = time.perf_counter() - t0
+    return len(pos) / el, len(pos), el
 
 
 def run_reference_other(args, rank, world):
@@ -1141,9 +1201,6 @@ def run_reference_other(args, rank, world):
     oracle of the same step on a bounded sample of the same catalogue."""
     if rank != 0:
         return
-    from oracle import fit as ofit
-    from oracle import force as oforce
-    from oracle import pm as opm
     per = []
     sample_n = 32 ** 3 if args.workload == "step256" else 64 ** 3
     for k in range(args.warmup + args.steps):
@@ -1152,16 +1209,7 @@ def run_reference_other(args, rank, world):
         elif args.workload == "fof256":
             rate, cn, _ = cpu_fof_sample(sample_n, args.fof_b)
         else:
-            pos, box, sigma = _pm_inputs(sample_n)
-            from workloads import configs as wc
-            prm = wc.CONFIGS["clustered256"]
-            c = ofit.fit_poly(prm["rc"], sigma, prm["eps"])
-            t0 = time.perf_counter()
-            oforce.accel_kdtree(pos, box, prm["rc"], prm["eps"], c)
-            opm.power_spectrum(pos, box, int(round(len(pos) ** (1 / 3))))
-            opm.pm_accel(pos, box, int(round(len(pos) ** (1 / 3))), sigma)
-            cn = len(pos)
-            rate = cn / (time.perf_counter() - t0)
+            rate, cn, _ = cpu_step_sample(sample_n)
         per.append(rate)
     value = float(np.mean(per[args.warmup:]))
     line = {
