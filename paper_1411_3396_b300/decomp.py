@@ -109,7 +109,9 @@ class Slabs:
         counts = torch.tensor([0 if s is None else len(s) for s in sends], dtype=torch.int64, device=dev)
         table = [torch.zeros_like(counts) for _ in range(world)]
         dist.all_gather(table, counts, group=group)
-        recv_pos, recv_ids, reqs = [], [], []
+        # one batch of point-to-point operations (grouped, so that NCCL does
+        # not block on the first receive while its peer waits on its own)
+        recv_pos, recv_ids, ops = [], [], []
         for q in range(world):
             if q == rank:
                 continue
@@ -119,15 +121,14 @@ class Slabs:
             recv_pos.append(rp)
             recv_ids.append(ri)
             if nq:
-                reqs.append(dist.irecv(rp, src=q, group=group, tag=2 * q))
-                reqs.append(dist.irecv(ri, src=q, group=group, tag=2 * q + 1))
-        for q in range(world):
-            if q == rank or len(sends[q]) == 0:
-                continue
-            reqs.append(dist.isend(pos[sends[q]].contiguous(), dst=q, group=group, tag=2 * rank))
-            reqs.append(dist.isend(ids[sends[q]].contiguous(), dst=q, group=group, tag=2 * rank + 1))
-        for r in reqs:
-            r.wait()
+                ops.append(dist.P2POp(dist.irecv, rp, q, group))
+                ops.append(dist.P2POp(dist.irecv, ri, q, group))
+            if len(sends[q]):
+                ops.append(dist.P2POp(dist.isend, pos[sends[q]].contiguous(), q, group))
+                ops.append(dist.P2POp(dist.isend, ids[sends[q]].contiguous(), q, group))
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
         all_pos = torch.cat([pos] + recv_pos)
         all_ids = torch.cat([ids] + recv_ids)
         own = torch.cat([torch.ones(len(pos), dtype=torch.bool, device=dev)] +
