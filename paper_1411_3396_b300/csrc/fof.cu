@@ -296,7 +296,11 @@ __global__ void k_fof_roots(int n, int* parent, int* __restrict__ root, int* __r
     if (i >= n) return;
     const int r = find_root(parent, i, c, max_iter);
     root[i] = r;
-    atomicAdd(&size[r], 1);
+    // lanes with the same root add their count once (members of a group are
+    // often neighbours in caller order; one address would otherwise take a
+    // serialised atomic per member)
+    const unsigned peers = __match_any_sync(__activemask(), r);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&size[r], __popc(peers));
 }
 
 // flag[i] = 1 for the root of a halo; flag[n] = 0 (the scan's total).
