@@ -714,44 +714,48 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
 __global__ void __launch_bounds__(256) k_cost(const Args a, int max_chunks, unsigned* __restrict__ cost,
                                               unsigned long long* __restrict__ keys, int* __restrict__ vals) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= max_chunks) return;
     const int n_chunks = a.ccs[a.total_cells];
-    if (I >= n_chunks) {
+    unsigned long long cst = 0;
+    if (I < max_chunks && I >= n_chunks) {
         keys[I] = 255ull;
         vals[I] = I;
-        return;
-    }
-    const Item it = load_item(a, I);
-    const VolDev& V = a.vols[it.vol];
-    int c[3], olo[3], ohi[3];
-    cell_range(it, V, c, olo, ohi);
-    unsigned long long sum = 0;
-    for (int oz = olo[2]; oz <= ohi[2]; ++oz) {
-        int nz = c[2] + oz;
-        nz += nz < 0 ? V.n_c : (nz >= V.n_c ? -V.n_c : 0);
-        for (int oy = olo[1]; oy <= ohi[1]; ++oy) {
-            int ny = c[1] + oy;
-            ny += ny < 0 ? V.n_c : (ny >= V.n_c ? -V.n_c : 0);
-            for (int ox = olo[0]; ox <= ohi[0]; ++ox) {
-                int nx = c[0] + ox;
-                nx += nx < 0 ? V.n_c : (nx >= V.n_c ? -V.n_c : 0);
-                const int cell = V.cell_base + (nz * V.n_c + ny) * V.n_c + nx;
-                sum += (unsigned)(a.cell_start[cell + 1] - a.cell_start[cell]);
+    } else if (I < n_chunks) {
+        const Item it = load_item(a, I);
+        const VolDev& V = a.vols[it.vol];
+        int c[3], olo[3], ohi[3];
+        cell_range(it, V, c, olo, ohi);
+        unsigned long long sum = 0;
+        for (int oz = olo[2]; oz <= ohi[2]; ++oz) {
+            int nz = c[2] + oz;
+            nz += nz < 0 ? V.n_c : (nz >= V.n_c ? -V.n_c : 0);
+            for (int oy = olo[1]; oy <= ohi[1]; ++oy) {
+                int ny = c[1] + oy;
+                ny += ny < 0 ? V.n_c : (ny >= V.n_c ? -V.n_c : 0);
+                for (int ox = olo[0]; ox <= ohi[0]; ++ox) {
+                    int nx = c[0] + ox;
+                    nx += nx < 0 ? V.n_c : (nx >= V.n_c ? -V.n_c : 0);
+                    const int cell = V.cell_base + (nz * V.n_c + ny) * V.n_c + nx;
+                    sum += (unsigned)(a.cell_start[cell + 1] - a.cell_start[cell]);
+                }
             }
         }
+        cst = sum * (unsigned long long)it.cnt;
+        if (cst > 0xffffffffull) cst = 0xffffffffull;
+        cost[I] = (unsigned)cst;
+        // quarter-octave bucket of the cost, largest first
+        const unsigned long long x = cst + 1;
+        const int msb = 63 - __clzll((long long)x);
+        const int frac = msb >= 2 ? (int)((x >> (msb - 2)) & 3) : (int)((x << (2 - msb)) & 3);
+        int bucket = msb * 4 + frac;
+        if (bucket > 254) bucket = 254;
+        keys[I] = (unsigned long long)(254 - bucket);
+        vals[I] = I;
     }
-    unsigned long long cst = sum * (unsigned long long)it.cnt;
-    if (cst > 0xffffffffull) cst = 0xffffffffull;
-    cost[I] = (unsigned)cst;
-    atomicAdd(&a.ctr->cost_total, cst);
-    // quarter-octave bucket of the cost, largest first
-    const unsigned long long x = cst + 1;
-    const int msb = 63 - __clzll((long long)x);
-    const int frac = msb >= 2 ? (int)((x >> (msb - 2)) & 3) : (int)((x << (2 - msb)) & 3);
-    int bucket = msb * 4 + frac;
-    if (bucket > 254) bucket = 254;
-    keys[I] = (unsigned long long)(254 - bucket);
-    vals[I] = I;
+    // the total: a warp sum first, one atomic per warp (every lane of the
+    // launch is alive here; lanes past the chunks add 0)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cst += __shfl_xor_sync(kFull, cst, o);
+    if ((threadIdx.x & 31) == 0 && cst) atomicAdd(&a.ctr->cost_total, cst);
 }
 
 __global__ void __launch_bounds__(256) k_gather_g(const float* __restrict__ g, const int* __restrict__ slot_idx,
