@@ -3,7 +3,9 @@
 // longest-first work ordering.
 //
 // Radix pass = histogram per 2048-key tile -> exclusive scan of the
-// digit-major histogram -> stable scatter.  Stability inside a tile: warp w
+// digit-major histogram -> stable scatter (the tile is first placed in
+// digit order in shared memory, so that the global writes of each digit's
+// run are contiguous).  Stability inside a tile: warp w
 // owns keys [256w, 256w+256) and walks them in rounds of 32; lanes holding
 // the same digit find each other with __match_any_sync, rank by lane order,
 // and a warp-private digit histogram in shared memory carries counts across
@@ -98,6 +100,10 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
     constexpr int kWarps = kScanThreads / 32;
     __shared__ int wh[kWarps][kRadixBuckets];
     __shared__ int gbase[kRadixBuckets];
+    __shared__ int loff[kRadixBuckets];
+    __shared__ int wsum[kWarps];
+    __shared__ unsigned long long skey[kScanTile];
+    __shared__ int sval[kScanTile];
     for (int i = threadIdx.x; i < kWarps * kRadixBuckets; i += blockDim.x) (&wh[0][0])[i] = 0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -120,24 +126,50 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
         rnk[r] = old + __popc(peers & lt);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) {
-        int run = 0;
+    // one digit per thread: prefix over the warps, the tile's count of the
+    // digit, and (block scan) the digit's first position inside the tile
+    static_assert(kRadixBuckets == kScanThreads, "one digit per thread");
+    const int d = threadIdx.x;
+    int run = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const int t = wh[w][d];
-            wh[w][d] = run;
-            run += t;
-        }
-        gbase[d] = hist_scan[(long long)d * n_tiles + blockIdx.x];
+    for (int w = 0; w < kWarps; ++w) {
+        const int t = wh[w][d];
+        wh[w][d] = run;
+        run += t;
+    }
+    gbase[d] = hist_scan[(long long)d * n_tiles + blockIdx.x];
+    const int incl = warp_inclusive_scan(run);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < kWarps ? wsum[lane] : 0;
+        v = warp_inclusive_scan(v);
+        if (lane < kWarps) wsum[lane] = v;
     }
     __syncthreads();
+    loff[d] = (warp > 0 ? wsum[warp - 1] : 0) + incl - run;
+    __syncthreads();
+    // the tile in digit order in shared memory (the same order as the
+    // global output: warp, round, lane within each digit) ...
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         if (dig[r] < kRadixBuckets) {
-            const int pos = gbase[dig[r]] + wh[warp][dig[r]] + rnk[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            const int lp = loff[dig[r]] + wh[warp][dig[r]] + rnk[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
         }
+    }
+    __syncthreads();
+    // ... then written out by consecutive threads to consecutive addresses
+    // of each digit's run
+    const long long tile0 = (long long)blockIdx.x * kScanTile;
+    const int cnt = (int)(n - tile0 < kScanTile ? n - tile0 : kScanTile);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const unsigned long long k = skey[t];
+        const int dd = (int)((k >> shift) & (kRadixBuckets - 1));
+        const int pos = gbase[dd] + (t - loff[dd]);
+        kout[pos] = k;
+        vout[pos] = sval[t];
     }
 }
 
