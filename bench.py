@@ -79,7 +79,9 @@ def cpu_oracle_sample(pos, box, prm, n_rows, seed, cores, reps=1):
     with ctx.Pool(cores) as pool:
         for _ in range(reps):
             rows = rng.choice(len(pos), n_rows, replace=False)
-            parts = np.array_split(rows, cores * 4)
+            # one call per worker: each call of the oracle's row function
+            # re-wraps the whole position array, a fixed cost per call
+            parts = np.array_split(rows, cores)
             t0 = time.perf_counter()
             out = pool.map(_cpu_rows, parts)
             el = time.perf_counter() - t0
@@ -1433,7 +1435,7 @@ def main():
     ap.add_argument("--n-particles", type=int, default=0,
                     help="resize the workload (box scaled to keep density 1); 0 = as named")
     ap.add_argument("--cpu-rows", type=int, default=24576)
-    ap.add_argument("--ref-rows", type=int, default=256)
+    ap.add_argument("--ref-rows", type=int, default=2048)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--n-grid", type=int, default=0, help="PM mesh points per axis (0 = cube root of n)")
     ap.add_argument("--fof-b", type=float, default=0.168, help="FOF linking length in mean spacings")
