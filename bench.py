@@ -1435,7 +1435,7 @@ def main():
     ap.add_argument("--n-particles", type=int, default=0,
                     help="resize the workload (box scaled to keep density 1); 0 = as named")
     ap.add_argument("--cpu-rows", type=int, default=24576)
-    ap.add_argument("--ref-rows", type=int, default=2048)
+    ap.add_argument("--ref-rows", type=int, default=8192)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--n-grid", type=int, default=0, help="PM mesh points per axis (0 = cube root of n)")
     ap.add_argument("--fof-b", type=float, default=0.168, help="FOF linking length in mean spacings")
