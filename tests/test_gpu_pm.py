@@ -103,6 +103,30 @@ def test_pm_accelerations_match_oracle(clustered, ng):
     p.close()
 
 
+def test_mesh_spacing_not_a_power_of_two():
+    # box 20 on a 16^3 mesh: d = 1.25, so n / L is not a power of two and the
+    # CIC kernels place particles with binary64 arithmetic; positions include
+    # values outside [0, L) (folded) and exactly on cell walls
+    L, ng, sigma = 20.0, 16, 0.8
+    pos, _, _ = gen.nfw_clustered(6000, L, 33, m_lo=40.0, m_hi=900.0)
+    pos = pos.copy()
+    pos[:4] = [[0.0, 1.25, 2.5], [L - 1e-12, 10.0, 5.0], [-0.625, 3.0, 21.25], [1.25 * 7, 1.25 * 3, 1.25 * 15]]
+    p = _pm(ng, L, sigma, len(pos))
+    x = torch.from_numpy(pos).cuda()
+    p.deposit(x)
+    counts = p.export("counts").cpu().numpy()
+    ref = opm.cic_deposit(pos, L, ng)
+    assert np.all(np.abs(counts - ref) <= 4e-7 * np.maximum(ref, 1.0))
+    k, pk, modes = (t.cpu().numpy() for t in p.power())
+    k_o, p_o, m_o = opm.power_spectrum(pos, L, ng)
+    np.testing.assert_array_equal(modes, m_o)
+    assert np.max(np.abs(pk - p_o) / p_o) <= PK_TOL
+    a = p.force(x).cpu().numpy()
+    rel = rel_errors(a[:, :3].astype(np.float64), opm.pm_accel(pos, L, ng, sigma))
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4
+    p.close()
+
+
 def test_lattice_on_grid_and_shot_noise():
     # a lattice on the grid points has delta = 0; uniform points have the
     # closed-form shot-noise level (checked against the oracle's value)
