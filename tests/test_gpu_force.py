@@ -120,6 +120,21 @@ def test_plain_kernel_matches_oracle(small_case):
     assert_force_close(acc, a_ref, name + " plain")
 
 
+def test_force_of_unwrapped_positions():
+    # positions anywhere in [-L, 2L) are folded by the binning: the forces of
+    # periodic images of the set match the oracle's forces of the set
+    w = _work("clustered256")
+    (pos, box), = w["volumes"]
+    rng = np.random.default_rng(21)
+    shifted = pos + rng.choice([-1.0, 0.0, 1.0], size=pos.shape) * box
+    shifted = np.where(shifted < -box, shifted + box, shifted)
+    shifted = np.where(shifted >= 2 * box, shifted - box, shifted)
+    plan, acc, _, _ = _gpu([(shifted, box)], w["params"], count=False)
+    a_ref, _ = oracle_force([(pos, box)], w["params"])
+    assert_force_close(acc, a_ref, "unwrapped positions")
+    plan.close()
+
+
 def test_force_is_deterministic():
     w = _work("clustered256")
     pos = torch.from_numpy(np.concatenate([p for p, _ in w["volumes"]])).cuda()

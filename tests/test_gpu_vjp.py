@@ -37,6 +37,26 @@ def test_vjp_matches_oracle(name, chunk):
     assert_force_close(xbar, ref, f"vjp {name}")
 
 
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_vjp_on_a_batch_plan(chunk):
+    # a batch of independent volumes (per-item constants in the packed loop):
+    # each volume's rows against the oracle's VJP of that volume alone
+    w = wc.make_workload(wc.small_variant("batch64"))
+    vols, prm = w["volumes"], w["params"]
+    pos = np.concatenate([p for p, _ in vols])
+    plan = make_plan(vols, prm, chunk_size=chunk)
+    plan.bin(torch.from_numpy(pos).cuda())
+    g = _g(len(pos), 11)
+    xbar = to_np(plan.vjp(torch.from_numpy(g).cuda()))
+    c = ofit.fit_poly(prm["rc"], prm["sigma"], prm["eps"])
+    off = 0
+    for p, box in vols:
+        n = len(p)
+        ref = oint.force_vjp(p, box, prm["rc"], prm["eps"], c, g[off:off + n, :3].astype(np.float64))
+        assert_force_close(xbar[off:off + n], ref, f"vjp batch volume of {n}")
+        off += n
+
+
 def test_vjp_scale_and_accumulate():
     w = wc.make_workload(wc.small_variant("uniform4k"))
     (pos, box), = w["volumes"]
