@@ -64,6 +64,37 @@ def test_leapfrog_matches_oracle():
     assert np.all(np.abs(inv[0:3] - v0.sum(axis=0)) < 1e-4 * np.abs(v0).sum())
 
 
+def test_leapfrog_on_a_batch_plan():
+    # independent volumes of different sides in one plan: each volume's
+    # trajectory (drift folded into its own box) against the oracle's
+    w = wc.make_workload(wc.small_variant("batch64"))
+    vols, prm = w["volumes"], w["params"]
+    pos = np.concatenate([p for p, _ in vols])
+    n = len(pos)
+    steps, dt = 5, 0.02
+    v0 = 0.1 * w["velocities"]
+    plan = make_plan(vols, prm)
+    x = torch.from_numpy(pos).cuda()
+    v = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    v[:, :3] = torch.from_numpy(v0).float()
+    acc = torch.empty_like(v)
+    plan.bin(x)
+    plan.force(acc)
+    plan.leapfrog(x, v, acc, dt, steps)
+    plan.status()
+    c = ofit.fit_poly(prm["rc"], prm["sigma"], prm["eps"])
+    xg, vg = to_np(x), to_np(v)[:, :3]
+    off = 0
+    for p, box in vols:
+        m = len(p)
+        xr, vr, _ = oint.leapfrog(p, v0[off:off + m], box, prm["rc"], prm["eps"], c, dt, steps)
+        assert np.all((xg[off:off + m] >= 0) & (xg[off:off + m] < box))
+        assert np.max(np.abs(oforce.min_image(xg[off:off + m] - xr, box))) < 1e-5
+        rv = rel_errors(vg[off:off + m], vr)
+        assert np.median(rv) <= 1e-5 and rv.max() <= 1e-3, (np.median(rv), rv.max())
+        off += m
+
+
 def test_leapfrog_zero_steps_is_identity():
     w = wc.make_workload(wc.small_variant("uniform4k"))
     (pos, box), = w["volumes"]
