@@ -173,8 +173,9 @@ int sr_bin(sr_plan* plan, const double* pos, int64_t n, void* stream);
  * particles are written).  One persistent launch: each warp repeatedly takes
  * the next chunk from the longest-first order, culls neighbour chunks and
  * particles by bounding boxes, stages the survivors through shared memory
- * and accumulates per-32-neighbour binary32 partial sums into a Kahan
- * (compensated) sum.  No float atomics: results are run-to-run identical.
+ * and accumulates per-batch binary32 partial sums (32 neighbours; 128 in the
+ * packed loop) into a Kahan (compensated) sum.  No float atomics: results
+ * are run-to-run identical.
  * acc: device, n rows float4 (written, caller order).
  * pair_count: device uint64, nullable: if given, the kernel also counts the
  *   ordered in-range pairs (i != j) under the binary32 predicate
@@ -232,7 +233,7 @@ int sr_force_plain(sr_plan* plan, float* acc, void* stream);
  * or added to (accumulate = 1).  Plans with 32-particle chunks run the
  * packed two-wide binary32 pair loop (each term the same binary32
  * operations as the scalar loop; even and odd neighbours summed separately
- * over batches of 64 before the compensated update); 64-particle chunks the
+ * over batches of 128 before the compensated update); 64-particle chunks the
  * scalar loop.  Deterministic.
  * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG (null pointers while the plan holds particles).
  */
@@ -323,9 +324,10 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  *   7:    as 2, with split partial sums;
  *   8..11: packed two-wide binary32 pair loop (split partial sums),
  *         launch shapes as 1, 2, 4, 3.
- * Variants 0..6 are bit-identical; so are 7..11.  Split partial sums add
- * even and odd neighbours of a 32-neighbour batch separately before the
- * compensated update, so 7..11 differ from 0..6 in the last bits.
+ * Variants 0..6 are bit-identical (batches of 32 neighbours); so are 8..11
+ * (packed, batches of 128).  Split partial sums add even and odd neighbours
+ * of a batch separately before the compensated update; variant 7 does so
+ * over batches of 32.  Variants of different groups differ in the last bits.
  * Plans with 64-particle chunks support variants 0..3.
  * Errors: SR_ERR_ARG (out of range or not available for the chunk size).
  */

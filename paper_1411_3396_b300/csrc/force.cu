@@ -37,7 +37,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreads = kWarpsPerBlock * 32;
-constexpr int kRing = 128;        // per-warp ring of staged neighbours (packed batches take 64)
+constexpr int kRing = 256;        // per-warp ring of staged neighbours (packed batches take 128)
 constexpr int kVjpMinBlocks = 1;   // VJP kernel: 256-thread blocks, at least this many per SM
 constexpr int vjp_flags(int k) { return k == 1 ? 2 : 0; }   // packed loop for 32-particle chunks
 
@@ -395,7 +395,8 @@ struct WarpState {
 // dependent FMA chain of the accumulation; summed before the Kahan update.
 // FLAGS bit 1: packed f32x2 pair loop over the pair-interleaved ring (see
 // ring_put); its partial sums split even / odd entries like bit 0, over
-// batches of 64 neighbours (one Kahan update per 64; 2% faster than 32).
+// batches of 128 neighbours (one Kahan update per 128; 64 was 2% faster
+// than 32, and 128 1% faster than 64).
 template <int MODE, int K, int FLAGS>
 __device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, float4* __restrict__ gring, int base,
                                                  int cnt, WarpState<MODE, K>& w, const PConsts& P) {
@@ -430,7 +431,16 @@ __device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, floa
         ZI[k] = f2_pack(w.z[k], w.z[k]);
         PX[k] = PY[k] = PZ[k] = 0ull;                // (+0, +0)
     }
-    if (MODE == kVjp) {
+    if (MODE != kVjp && npairs == 64) {
+#pragma unroll
+        for (int m = 0; m < 64; ++m) {
+            const ulonglong2 a = A[m0 + m];
+            const f2 z = B[m0 + m];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                pair_force2<CNT>(a.x, a.y, z, XI[k], YI[k], ZI[k], P, PX[k], PY[k], PZ[k], w.npair[k]);
+        }
+    } else if (MODE == kVjp) {
         const ulonglong2* G = reinterpret_cast<const ulonglong2*>(gring);
         const f2* Hz = reinterpret_cast<const f2*>(gring + kRing / 2);
         f2 GXI[K], GYI[K], GZI[K];
@@ -650,11 +660,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
                 }
                 w.wr += __popc(m);
                 __syncwarp();
-                if (w.wr - w.rd >= (PACKED ? 64 : 32)) {
+                if (w.wr - w.rd >= (PACKED ? 128 : 32)) {
                     const int base = w.rd & (kRing - 1);
-                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, rg, base, 64, w, PK);
+                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, rg, base, 128, w, PK);
                     else run_batch<MODE, K, FLAGS>(rp + base, rg + base, 32, w, KC);
-                    w.rd += PACKED ? 64 : 32;
+                    w.rd += PACKED ? 128 : 32;
                     __syncwarp();
                 }
             }
@@ -803,7 +813,7 @@ int occ(sr_plan* p) {
 //   0: 8 x 1   1: 8 x 2   2: 8 x 3   3: 8 x 4   (register budgets 255, 128, 85, 64)
 //   4: 4 x 6   5: 4 x 7   6: 4 x 8              (85, 73, 64)
 //   7: 8 x 3 with split partial sums (even / odd neighbours)
-//   8..11: packed f32x2 pair loop (split partial sums, batches of 64): 8 x 2, 8 x 3, 4 x 6, 8 x 4
+//   8..11: packed f32x2 pair loop (split partial sums, batches of 128): 8 x 2, 8 x 3, 4 x 6, 8 x 4
 // 64-particle chunks (K = 2) use variants 0..3 only.
 #define SR_FORCE_VARIANTS(X) \
     X(0, 8, 1, 0) X(1, 8, 2, 0) X(2, 8, 3, 0) X(3, 8, 4, 0) \

@@ -81,7 +81,7 @@ def test_pair_counts_bit_exact(small_case):
 
 def test_all_kernel_variants_give_identical_forces(small_case):
     # variants 0-6 share the summation order of the counting kernel; the
-    # packed two-wide variants 8-11 share theirs (batches of 64 neighbours,
+    # packed two-wide variants 8-11 share theirs (batches of 128 neighbours,
     # even and odd entries apart) and agree bit for bit; 7 (scalar split
     # sums, batches of 32) and all of them agree with the oracle
     from paper_1411_3396_b300 import SrError
