@@ -322,12 +322,14 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  *   4..6: 128-thread blocks, at least 6, 7, 8 resident per SM
  *         (register budgets 85, 73, 64);
  *   7:    as 2, with split partial sums;
- *   8..11: packed two-wide binary32 pair loop (split partial sums),
- *         launch shapes as 1, 2, 4, 3.
+ *   8..11: packed two-wide binary32 pair loop (split partial sums,
+ *         batches of 128 neighbours), launch shapes as 1, 2, 4, 3;
+ *   12:   the packed loop in batches of 64, launch shape as 3.
  * Variants 0..6 are bit-identical (batches of 32 neighbours); so are 8..11
  * (packed, batches of 128).  Split partial sums add even and odd neighbours
  * of a batch separately before the compensated update; variant 7 does so
- * over batches of 32.  Variants of different groups differ in the last bits.
+ * over batches of 32 and variant 12 over batches of 64.  Variants of
+ * different groups differ in the last bits.
  * Plans with 64-particle chunks support variants 0..3.
  * Errors: SR_ERR_ARG (out of range or not available for the chunk size).
  */
@@ -337,7 +339,7 @@ int sr_plan_set_variant(sr_plan* plan, int variant);
  * sr_autotune -- time each pair-kernel variant on the data of the last
  * sr_bin (reps launches each, CUDA events on stream, synchronising) and
  * keep the fastest.  acc: device float4 rows used as scratch output.
- * ms_out: host float[12], nullable, receives the mean time per variant
+ * ms_out: host float[13], nullable, receives the mean time per variant
  * (0 for variants not available for the plan's chunk size).
  * This is a set-up call: it synchronises and must not be captured.
  * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG, SR_ERR_CUDA.

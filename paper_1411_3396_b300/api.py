@@ -199,7 +199,7 @@ class Plan:
         fastest and returns the per-variant mean times (ms)."""
         n = self._need_binned()
         acc = torch.empty((n, 4), dtype=torch.float32, device="cuda")
-        ms = (ctypes.c_float * 12)()
+        ms = (ctypes.c_float * 13)()
         check(load().sr_autotune(self._h, _ptr(acc), int(reps), ms, _stream()))
         return list(ms)
 

@@ -400,6 +400,7 @@ struct WarpState {
 template <int MODE, int K, int FLAGS>
 __device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, float4* __restrict__ gring, int base,
                                                  int cnt, WarpState<MODE, K>& w, const PConsts& P) {
+    constexpr bool kFull128 = (FLAGS & 4) == 0;     // full batches hold 128 entries (else 64)
     constexpr bool CNT = MODE == kForceCount;
     const ulonglong2* A = reinterpret_cast<const ulonglong2*>(ring);
     const f2* B = reinterpret_cast<const f2*>(ring + kRing / 2);
@@ -431,7 +432,7 @@ __device__ __forceinline__ void run_batch_packed(float4* __restrict__ ring, floa
         ZI[k] = f2_pack(w.z[k], w.z[k]);
         PX[k] = PY[k] = PZ[k] = 0ull;                // (+0, +0)
     }
-    if (MODE != kVjp && npairs == 64) {
+    if (MODE != kVjp && kFull128 && npairs == 64) {
 #pragma unroll
         for (int m = 0; m < 64; ++m) {
             const ulonglong2 a = A[m0 + m];
@@ -588,6 +589,7 @@ template <int MODE, int K, int WARPS, int MINB, int FLAGS, bool SINGLE>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const VolDev v0) {
     constexpr int C = 32 * K;
     constexpr bool PACKED = (FLAGS & 2) != 0;
+    constexpr int kPackedBatch = (FLAGS & 4) ? 64 : 128;   // staged neighbours per packed batch
     __shared__ float4 ring_p[WARPS][kRing];
     __shared__ float4 ring_g[MODE == kVjp ? WARPS : 1][kRing];
     const int warp = threadIdx.x >> 5;
@@ -660,11 +662,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
                 }
                 w.wr += __popc(m);
                 __syncwarp();
-                if (w.wr - w.rd >= (PACKED ? 128 : 32)) {
+                if (w.wr - w.rd >= (PACKED ? kPackedBatch : 32)) {
                     const int base = w.rd & (kRing - 1);
-                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, rg, base, 128, w, PK);
+                    if (PACKED) run_batch_packed<MODE, K, FLAGS>(rp, rg, base, kPackedBatch, w, PK);
                     else run_batch<MODE, K, FLAGS>(rp + base, rg + base, 32, w, KC);
-                    w.rd += PACKED ? 128 : 32;
+                    w.rd += PACKED ? kPackedBatch : 32;
                     __syncwarp();
                 }
             }
@@ -814,11 +816,12 @@ int occ(sr_plan* p) {
 //   4: 4 x 6   5: 4 x 7   6: 4 x 8              (85, 73, 64)
 //   7: 8 x 3 with split partial sums (even / odd neighbours)
 //   8..11: packed f32x2 pair loop (split partial sums, batches of 128): 8 x 2, 8 x 3, 4 x 6, 8 x 4
+//   12: the packed loop in batches of 64, 8 x 4 (faster at near-uniform density)
 // 64-particle chunks (K = 2) use variants 0..3 only.
 #define SR_FORCE_VARIANTS(X) \
     X(0, 8, 1, 0) X(1, 8, 2, 0) X(2, 8, 3, 0) X(3, 8, 4, 0) \
     X(4, 4, 6, 0) X(5, 4, 7, 0) X(6, 4, 8, 0) X(7, 8, 3, 1) \
-    X(8, 8, 2, 3) X(9, 8, 3, 3) X(10, 4, 6, 3) X(11, 8, 4, 3)
+    X(8, 8, 2, 3) X(9, 8, 3, 3) X(10, 4, 6, 3) X(11, 8, 4, 3) X(12, 8, 4, 7)
 
 template <int K, bool SINGLE>
 int occupancy_k(sr_plan* p) {

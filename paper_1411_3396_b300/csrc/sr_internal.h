@@ -100,7 +100,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBuckets = 1 << kRadixBits;
-constexpr int kVariants = 12;       // force-kernel variants (launch shape / accumulation)
+constexpr int kVariants = 13;       // force-kernel variants (launch shape / accumulation)
 
 // Per-volume constants, device resident, read once per work item.
 // Lengths inside kernels are in units of the fine grid h = L / (n_c 2^b).

@@ -83,7 +83,8 @@ def test_all_kernel_variants_give_identical_forces(small_case):
     # variants 0-6 share the summation order of the counting kernel; the
     # packed two-wide variants 8-11 share theirs (batches of 128 neighbours,
     # even and odd entries apart) and agree bit for bit; 7 (scalar split
-    # sums, batches of 32) and all of them agree with the oracle
+    # sums, batches of 32), 12 (packed, batches of 64) and all of them agree
+    # with the oracle
     from paper_1411_3396_b300 import SrError
     name, w, chunk = small_case
     plan, acc_c, _, _ = _gpu(w["volumes"], w["params"], count=True, chunk_size=chunk)
@@ -108,6 +109,8 @@ def test_all_kernel_variants_give_identical_forces(small_case):
             packed = acc
             assert_force_close(acc, a_ref, f"{name} variant {v}")
         assert acc.tobytes() == packed.tobytes(), f"variant {v}"
+    plan.set_variant(12)                      # the packed loop in batches of 64
+    assert_force_close(to_np(plan.force()), a_ref, f"{name} variant 12")
 
 
 def test_plain_kernel_matches_oracle(small_case):
