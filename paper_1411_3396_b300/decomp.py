@@ -68,6 +68,11 @@ class Slabs:
         q = torch.clamp(torch.floor(x / self.h), max=self.M - 1).to(torch.int64)
         return q >> self.sub_bits
 
+    def owner(self, pos: torch.Tensor) -> torch.Tensor:
+        """Rank whose slab holds each particle."""
+        starts = torch.tensor([c0 for c0, _ in self.bounds[1:]], dtype=torch.int64, device=pos.device)
+        return torch.bucketize(self.cell_x(pos), starts, right=True)
+
     def owned(self, pos: torch.Tensor, rank: int) -> torch.Tensor:
         """Mask of the particles in rank's slab."""
         c0, c1 = self.bounds[rank]
@@ -135,3 +140,45 @@ class Slabs:
                         [torch.zeros(len(r), dtype=torch.bool, device=dev) for r in recv_ids])
         order = torch.argsort(all_ids)
         return all_pos[order].contiguous(), all_ids[order].contiguous(), own[order].contiguous()
+
+    def migrate(self, pos: torch.Tensor, ids: torch.Tensor, *fields: torch.Tensor, group=None):
+        """Hand every particle to the rank whose slab holds it, after a drift
+        has moved particles across slab faces (any number of slabs, positions
+        within one period of [0, box)).  `fields` are per-particle arrays
+        (velocities, accelerations, ...) that travel with the positions.
+        Returns (pos, ids, *fields) of the particles this rank owns, in
+        increasing global-id order.  One all-gather of the send counts, then
+        one batch of point-to-point sends to the ranks that gain particles."""
+        import torch.distributed as dist
+        world = dist.get_world_size(group)
+        rank = dist.get_rank(group)
+        if world != self.world:
+            raise ValueError("slab count differs from the process group size")
+        if any(len(f) != len(pos) for f in fields) or len(ids) != len(pos):
+            raise ValueError("ids and fields need one row per particle")
+        dev = pos.device
+        dest = self.owner(pos)
+        arrays = (pos, ids) + fields
+        sends = [torch.nonzero(dest == q).squeeze(1) for q in range(world)]
+        counts = torch.tensor([0 if q == rank else len(sends[q]) for q in range(world)],
+                              dtype=torch.int64, device=dev)
+        table = [torch.zeros_like(counts) for _ in range(world)]
+        dist.all_gather(table, counts, group=group)
+        kept = [a[sends[rank]] for a in arrays]
+        recv, ops = [], []
+        for q in range(world):
+            if q == rank:
+                continue
+            nq = int(table[q][rank].item())
+            bufs = [torch.empty((nq,) + tuple(a.shape[1:]), dtype=a.dtype, device=dev) for a in arrays]
+            recv.append(bufs)
+            if nq:
+                ops += [dist.P2POp(dist.irecv, b, q, group) for b in bufs]
+            if len(sends[q]):
+                ops += [dist.P2POp(dist.isend, a[sends[q]].contiguous(), q, group) for a in arrays]
+        if ops:
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
+        out = [torch.cat([kept[k]] + [b[k] for b in recv]) for k in range(len(arrays))]
+        order = torch.argsort(out[1])
+        return tuple(a[order].contiguous() for a in out)

@@ -3,7 +3,8 @@ slab bounds, cell membership against the oracle's binning, owned sets that
 partition the volume, ghost shells of exactly the neighbouring cells, and the
 point-to-point exchange between gloo ranks (world sizes 2 and 3), which must
 hand every rank the same owned + ghost set as a selection from the whole
-array."""
+array, and the migration of drifted particles (with the fields that travel
+with them) to their new owners over several steps."""
 import multiprocessing as mp
 import os
 import socket
@@ -75,6 +76,17 @@ def test_owned_partition_and_ghost_shell(world):
     np.testing.assert_array_equal(owners, np.ones(len(pos), dtype=np.int64))
 
 
+def test_owner_matches_owned_masks():
+    from paper_1411_3396_b300.decomp import Slabs
+    box = 24.0
+    x = torch.from_numpy(_clustered(box=box))
+    for n_c, world in [(6, 1), (6, 4), (7, 3), (5, 5)]:
+        s = Slabs(box, n_c, 2, world)
+        own = s.owner(x)
+        for r in range(world):
+            assert torch.equal(own == r, s.owned(x, r))
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -120,3 +132,55 @@ def test_exchange_gloo(world):
     assert all(ok for _, ok, _, _ in res)
     assert sum(n_own for _, _, n_own, _ in res) == 6000
     assert all(n_loc > n_own for _, _, n_own, n_loc in res)
+
+
+def _migrate_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+    from paper_1411_3396_b300.decomp import Slabs
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        box, n_c = 24.0, 8
+        pos = torch.from_numpy(_clustered(box=box))
+        n = len(pos)
+        ids = torch.arange(n, dtype=torch.int64)
+        vel = torch.from_numpy(np.random.default_rng(9).normal(size=(n, 4)).astype(np.float32))
+        s = Slabs(box, n_c, 1, world)
+        mine = s.owned(pos, rank)
+        p, i, v = pos[mine], ids[mine], vel[mine]
+        ok, moved = True, 0
+        for step in range(4):
+            # the same displacement field on every rank (drawn for all ids),
+            # up to 1.5 slab widths, so particles also skip a rank
+            g = np.random.default_rng(100 + step).uniform(-9.0, 9.0, size=(n, 3))
+            disp = torch.from_numpy(g)
+            p = torch.remainder(p + disp[i], box)
+            pos = torch.remainder(pos + disp, box)
+            moved += int((s.owner(p) != rank).sum())
+            p, i, v = s.migrate(p, i, v)
+            want = s.owned(pos, rank)
+            ok &= torch.equal(i, ids[want]) and torch.equal(p, pos[want]) and torch.equal(v, vel[want])
+            got = s.exchange(p, i)
+            ok &= all(torch.equal(a, b) for a, b in zip(got, s.local_set(pos, ids, rank)))
+        q.put((rank, bool(ok), len(i), moved))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_migrate_gloo(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_migrate_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok, _, _ in res), res
+    assert sum(n for _, _, n, _ in res) == 6000
+    assert all(m > 0 for _, _, _, m in res)
