@@ -1295,7 +1295,7 @@ def run_diff(args, rank, world, local_rank):
     def eager(xi, vi):
         x = xi.detach().clone().requires_grad_(True)
         v = vi.detach().clone().requires_grad_(True)
-        xk, vk = trajectory(plan, x, v, steps, dt)
+        xk, vk = trajectory(traj_plans, x, v, steps, dt)
         loss = loss_fn(xk, vk)
         loss.backward()
         return loss, x.grad, v.grad
@@ -1318,6 +1318,15 @@ def run_diff(args, rank, world, local_rank):
     else:
         plan.bin(xd)
         plan.autotune(reps=2)
+    # one plan per substep (each substep binned once, its binning kept for
+    # the backward sweep), unless --shared-plan (binned again backwards)
+    traj_plans = plan
+    if not args.shared_plan and steps > 1:
+        variant = plan.info()["variant"]
+        traj_plans = [plan] + [Plan(box, cfg["rc"], cfg["eps"], cfg["sigma"], n, chunk_size=args.chunk_size)
+                               for _ in range(steps - 1)]
+        for p in traj_plans[1:]:
+            p.set_variant(variant)
     # eager trajectories (autograd issuing every launch from the host), then
     # the same sweep captured once in a CUDA graph and replayed
     for _ in range(args.warmup):
@@ -1333,7 +1342,7 @@ def run_diff(args, rank, world, local_rank):
     if args.no_graph:
         one = eager
     else:
-        tg = TrajectoryGraph(plan, xd, vd, steps, dt, loss_fn)
+        tg = TrajectoryGraph(traj_plans, xd, vd, steps, dt, loss_fn)
 
         def one(xi, vi):
             return tg.run(xi, vi)
@@ -1412,6 +1421,8 @@ def run_diff(args, rank, world, local_rank):
                    "pairs_forward": pairs, "pairs_per_step": total_pairs,
                    "trajectories_per_s": 1e3 / ms, "loss": float(loss.item()),
                    "graph": not args.no_graph, "eager_ms_per_step": eager_ms,
+                   "plans": 1 if isinstance(traj_plans, Plan) else len(traj_plans),
+                   "binnings_per_trajectory": steps if not isinstance(traj_plans, Plan) else 2 * steps,
                    "parallelism": "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
@@ -1447,6 +1458,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="diff64: time eager trajectories only")
+    ap.add_argument("--shared-plan", action="store_true",
+                    help="diff64: one plan for every substep (binned again in the backward sweep)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--variant", type=int, default=-1, help="force a pair-kernel variant (skips autotuning)")

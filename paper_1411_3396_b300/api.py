@@ -84,6 +84,7 @@ class Plan:
         self.r_c, self.eps, self.sigma = float(r_c), float(eps), float(sigma)
         self.capacity = sum(self.volume_counts) if _batch is not None else int(n_max)
         self.n = None
+        self.binnings = 0           # calls that replaced the plan's binning
 
     @classmethod
     def batch(cls, boxes, counts, r_c, eps, sigma, fit_mode="constrained", n_cells=None,
@@ -120,6 +121,7 @@ class Plan:
         _need(pos, torch.float64, 3, "pos")
         check(load().sr_bin(self._h, _ptr(pos), pos.shape[0], _stream()))
         self.n = pos.shape[0]
+        self.binnings += 1
         return self
 
     def force(self, acc: torch.Tensor | None = None, count: bool = False, per_particle: bool = False):
@@ -152,6 +154,7 @@ class Plan:
         _need(acc, torch.float32, 4, "acc", n)
         check(load().sr_leapfrog(self._h, _ptr(pos), _ptr(vel), _ptr(acc), float(dt), int(steps), n, _stream()))
         self.n = n
+        self.binnings += 1
         return pos, vel, acc
 
     def force_plain(self, acc: torch.Tensor | None = None):
@@ -212,9 +215,11 @@ class Plan:
         check(load().sr_graph_capture(self._h, _ptr(pos), _ptr(vel), _ptr(acc), float(dt), pos.shape[0],
                                       _stream()))
         self.n = pos.shape[0]
+        self.binnings += 1
 
     def graph_launch(self):
         check(load().sr_graph_launch(self._h, _stream()))
+        self.binnings += 1
 
     def status(self):
         check(load().sr_plan_status(self._h, _stream()))
@@ -246,6 +251,7 @@ class Plan:
                                   c_void_p(acc.data_ptr()) if acc is not None else c_void_p(0),
                                   float(dt), n, _stream()))
         self.n = n
+        self.binnings += 1
 
     def _need_binned(self) -> int:
         if self.n is None:

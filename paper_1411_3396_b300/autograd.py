@@ -6,9 +6,12 @@
 
 in the library's kernels (sr_bin, sr_force, sr_kick, sr_drift) and returns
 (x_K, v_K).  Gradients flow to x0 and v0 through a hand-written reverse
-sweep: per-substep checkpointing keeps only x_k (the force depends on the
-positions alone); the backward pass re-bins x_k and applies, from the last
-substep to the first,
+sweep.  The force depends on the positions alone, so the sweep needs only
+each substep's binning of x_k: with one plan, per-substep checkpointing
+keeps x_k and the backward pass bins it again; with one plan per substep
+(a sequence of ``steps`` plans), substep k's binning stays in plan k and
+the backward pass reuses it (half the binnings, one plan's workspace per
+substep).  The sweep applies, from the last substep to the first,
 
     vbar += dt * xbar                 (adjoint of the drift)
     xbar += (da/dx)^T (dt * vbar)     (adjoint of the kick, sr_force_vjp)
@@ -24,37 +27,56 @@ import torch
 from .api import Plan, kick, launch_count
 
 
+def _plans(plan, steps: int):
+    """A tuple of one shared plan, or of one plan per substep."""
+    if isinstance(plan, Plan):
+        return (plan,)
+    plans = tuple(plan)
+    if len(plans) != steps or not all(isinstance(p, Plan) for p in plans):
+        raise ValueError("give one Plan, or a sequence of one Plan per substep")
+    return plans
+
+
 class _Trajectory(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x0, v0, plan: Plan, steps: int, dt: float):
+    def forward(ctx, x0, v0, plans, steps: int, dt: float):
         x = x0.detach().clone()
         v = v0.detach().clone()
         acc = torch.empty_like(v)
+        shared = len(plans) == 1
         checkpoints = []
-        for _ in range(steps):
-            checkpoints.append(x.clone())
+        for k in range(steps):
+            plan = plans[0] if shared else plans[k]
+            if shared:
+                checkpoints.append(x.clone())
             plan.bin(x)
             plan.force(acc)
             kick(acc, v, dt)
             plan.drift(x, v, dt)
         ctx.save_for_backward(*checkpoints)
-        ctx.plan, ctx.steps, ctx.dt = plan, steps, dt
+        ctx.plans, ctx.steps, ctx.dt = plans, steps, dt
+        ctx.binnings = [p.binnings for p in plans]
+        ctx.n, ctx.device = x0.shape[0], x0.device
         return x, v
 
     @staticmethod
     def backward(ctx, gx, gv):
-        plan, steps, dt = ctx.plan, ctx.steps, ctx.dt
+        plans, steps, dt = ctx.plans, ctx.steps, ctx.dt
         checkpoints = ctx.saved_tensors
-        n = checkpoints[0].shape[0]
-        xbar = torch.zeros((n, 4), dtype=torch.float32, device=checkpoints[0].device)
+        shared = len(plans) == 1
+        if not shared and [p.binnings for p in plans] != ctx.binnings:
+            raise RuntimeError("a substep's plan was binned again between the forward and the backward pass")
+        xbar = torch.zeros((ctx.n, 4), dtype=torch.float32, device=ctx.device)
         if gx is not None:
             xbar[:, :3] = gx.to(torch.float32)
-        vbar = torch.zeros((n, 4), dtype=torch.float32, device=xbar.device)
+        vbar = torch.zeros((ctx.n, 4), dtype=torch.float32, device=ctx.device)
         if gv is not None:
             vbar.copy_(gv.to(torch.float32))
         for k in range(steps - 1, -1, -1):
             kick(xbar, vbar, dt)                                   # vbar += dt * xbar
-            plan.bin(checkpoints[k])
+            if shared:
+                plans[0].bin(checkpoints[k])
+            plan = plans[0] if shared else plans[k]
             plan.vjp(vbar, xbar, g_scale=dt, accumulate=True)      # xbar += J^T (dt vbar)
         gx0 = xbar[:, :3].to(torch.float64)
         gv0 = vbar.clone()
@@ -62,15 +84,21 @@ class _Trajectory(torch.autograd.Function):
         return gx0, gv0, None, None, None
 
 
-def trajectory(plan: Plan, x0: torch.Tensor, v0: torch.Tensor, steps: int, dt: float):
-    """(x_K, v_K) after ``steps`` kick-drift substeps; differentiable in x0, v0."""
-    return _Trajectory.apply(x0, v0, plan, int(steps), float(dt))
+def trajectory(plan, x0: torch.Tensor, v0: torch.Tensor, steps: int, dt: float):
+    """(x_K, v_K) after ``steps`` kick-drift substeps; differentiable in x0, v0.
+
+    ``plan`` is one Plan (binned again in the backward pass) or a sequence of
+    ``steps`` Plans of the same parameters and kernel variant (substep k
+    binned once, in plan k).  The gradients are the same bits either way."""
+    steps = int(steps)
+    return _Trajectory.apply(x0, v0, _plans(plan, steps), steps, float(dt))
 
 
 class TrajectoryGraph:
     """A trajectory, a scalar loss on its end state and the gradient sweep,
     captured once in a CUDA graph and replayed.
 
+    ``plan`` is one Plan or one per substep, as for ``trajectory``.
     ``loss_fn(x_K, v_K)`` returns a scalar tensor.  Each ``run(x0, v0)``
     copies the inputs into the graph's static buffers and replays the
     captured kernels (the same kernels in the same order as the eager
@@ -81,7 +109,7 @@ class TrajectoryGraph:
     path are capture-safe: they neither allocate nor synchronise.
     """
 
-    def __init__(self, plan: Plan, x0: torch.Tensor, v0: torch.Tensor, steps: int, dt: float, loss_fn,
+    def __init__(self, plan, x0: torch.Tensor, v0: torch.Tensor, steps: int, dt: float, loss_fn,
                  warmup: int = 2):
         self.plan, self.steps, self.dt, self.loss_fn = plan, int(steps), float(dt), loss_fn
         self.x = x0.detach().clone().requires_grad_(True)

@@ -196,3 +196,55 @@ def test_trajectory_graph_is_bit_identical_to_eager():
         torch.cuda.synchronize()
         for a, b in zip(got, ref):
             assert torch.equal(a, b)
+
+
+def test_per_substep_plans_give_the_shared_plans_bits():
+    # one plan per substep keeps each substep's binning for the backward
+    # sweep instead of binning it again: the same gradients, eager and
+    # replayed in a graph, with fewer kernels per replay
+    from paper_1411_3396_b300 import TrajectoryGraph, trajectory
+    w = wc.make_workload(wc.small_variant("diff64"))
+    (pos, box), = w["volumes"]
+    prm = w["params"]
+    steps, dt = 4, prm["dt"]
+    shared = make_plan(w["volumes"], prm)
+    per = [make_plan(w["volumes"], prm) for _ in range(steps)]
+    n = len(pos)
+    rng = np.random.default_rng(21)
+    target = torch.from_numpy(np.mod(pos + rng.normal(0, 0.2, pos.shape), box)).cuda()
+
+    def loss_fn(xk, vk):
+        d = xk - target
+        d = d - box * torch.round(d / box)
+        return (d * d).sum() + 0.5 * (vk[:, :3].double() ** 2).sum()
+
+    def grads(plans, x0, v0):
+        x = x0.clone().requires_grad_(True)
+        v = v0.clone().requires_grad_(True)
+        xk, vk = trajectory(plans, x, v, steps, dt)
+        loss = loss_fn(xk, vk)
+        gx, gv = torch.autograd.grad(loss, (x, v))
+        return loss.detach(), gx, gv, xk.detach(), vk.detach()
+
+    x0 = torch.from_numpy(pos).cuda()
+    v0 = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    v0[:, :3] = torch.from_numpy(rng.normal(0, 0.3, (n, 3))).float().cuda()
+    ref = grads(shared, x0, v0)
+    got = grads(per, x0, v0)
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    g_per = TrajectoryGraph(per, x0, v0, steps, dt, loss_fn)
+    g_shared = TrajectoryGraph(shared, x0, v0, steps, dt, loss_fn)
+    for a, b in zip(g_per.run(x0, v0), ref[:3]):
+        assert torch.equal(a, b)
+    assert g_per.kernels < g_shared.kernels
+    # a plan binned again between the passes is refused, as is a plan list
+    # of the wrong length
+    x = x0.clone().requires_grad_(True)
+    v = v0.clone().requires_grad_(True)
+    xk, vk = trajectory(per, x, v, steps, dt)
+    per[1].bin(x0)
+    with pytest.raises(RuntimeError):
+        torch.autograd.grad(loss_fn(xk, vk), (x, v))
+    with pytest.raises(ValueError):
+        trajectory(per[:2], x, v, steps, dt)
