@@ -338,9 +338,12 @@ int sr_plan_set_variant(sr_plan* plan, int variant);
 /*
  * sr_autotune -- time each pair-kernel variant on the data of the last
  * sr_bin (reps launches each, CUDA events on stream, synchronising) and
- * keep the fastest.  acc: device float4 rows used as scratch output.
+ * keep the fastest.  When the second fastest is within 3% of it, the two
+ * are timed again, one launch of each in turn over 2 reps + 1 rounds, and
+ * the faster total is kept.  acc: device float4 rows used as scratch output.
  * ms_out: host float[13], nullable, receives the mean time per variant
- * (0 for variants not available for the plan's chunk size).
+ * of the first pass (0 for variants not available for the plan's chunk
+ * size).
  * This is a set-up call: it synchronises and must not be captured.
  * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG, SR_ERR_CUDA.
  */

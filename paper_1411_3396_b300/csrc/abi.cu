@@ -100,7 +100,7 @@ int make_volume(const sr_params& q, const double coef[6], int b, int cell_base, 
     V->h = h;
     int ex = 0;
     V->h_pow2 = (std::frexp(h, &ex) == 0.5) ? 1 : 0;
-    V->inv_h = V->h_pow2 ? 1.0 / h : 0.0;
+    V->inv_h = 1.0 / h;        // RN(1/h): exact scale when h = 2^k, else the binning's quotient correction
     V->inv_h_exp = V->h_pow2 ? 1 - ex : 0;            // h = 2^(ex - 1)
     const double h2 = h * h;
     const double e64 = q.eps * q.eps;
@@ -509,10 +509,11 @@ int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
     cudaEvent_t e0, e1;
     SR_CUDA_CHECK(cudaEventCreate(&e0));
     SR_CUDA_CHECK(cudaEventCreate(&e1));
-    float best = 1e30f;
+    float best = 1e30f, msv[kVariants];
     int best_v = p->variant;
     int rc = SR_OK;
     for (int v = 0; v < kVariants && rc == SR_OK; ++v) {
+        msv[v] = 0.f;
         if (ms_out) ms_out[v] = 0.f;
         if (p->force_blocks_v[v] <= 0) continue;       // not built for this chunk size
         p->variant = v;
@@ -525,8 +526,34 @@ int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= reps;
+        msv[v] = ms;
         if (ms_out) ms_out[v] = ms;
         if (ms < best) { best = ms; best_v = v; }
+    }
+    // The two fastest variants are often within the run-to-run spread of a
+    // single timing (about 1%): when they are within 3%, time them again,
+    // alternating one launch of each over 2 reps + 1 rounds, so that clock
+    // or power drift weighs on both alike, and keep the faster total.
+    int second = -1;
+    for (int v = 0; v < kVariants && rc == SR_OK; ++v)
+        if (v != best_v && msv[v] > 0.f && (second < 0 || msv[v] < msv[second])) second = v;
+    if (rc == SR_OK && second >= 0 && msv[second] < 1.03f * best) {
+        const int cand[2] = {best_v, second};
+        float tot[2] = {0.f, 0.f};
+        for (int r = 0; r < 2 * reps + 1 && rc == SR_OK; ++r) {
+            for (int c = 0; c < 2 && rc == SR_OK; ++c) {
+                p->variant = cand[c];
+                cudaEventRecord(e0, st);
+                rc = launch_force(p, acc, nullptr, nullptr, st);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "sr_autotune"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tot[c] += ms;
+            }
+        }
+        if (rc == SR_OK && tot[1] < tot[0]) best_v = second;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

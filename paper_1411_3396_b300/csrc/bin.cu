@@ -47,6 +47,22 @@ __device__ __forceinline__ int volume_of_cell(int cell, const int* __restrict__ 
     return lo;
 }
 
+// x / h correctly rounded in binary64, for x in [0, box) and y = RN(1/h),
+// by Markstein's fused multiply-add quotient correction (P. Markstein, IBM
+// J. Res. Dev. 34(1), 1990).  The product x y can be 1.5 ulp from x / h,
+// so one correction step first brings q within an ulp.  After that the
+// residual x - h q is exact, and q + (x - h q) y rounds to the correctly
+// rounded quotient.  Five binary64 operations replace a division; B300's
+// binary64 rate makes that the cost of binning when h is not a power of
+// two.  Below 2^-900 the residual could leave the normal range, so the
+// division is taken there (x = 0 included).
+__device__ __forceinline__ double quotient_rn(double x, double h, double y) {
+    if (x < 0x1p-900) return x / h;
+    double q = x * y;
+    q = fma(fma(-q, h, x), y, q);
+    return fma(fma(-q, h, x), y, q);
+}
+
 // Fine-grid coordinate of one axis; flags non-finite / out-of-range input.
 __device__ __forceinline__ void fine_axis(double x, const VolDev& V, double& t, int& q, bool& bad) {
     const double box = V.box;
@@ -58,7 +74,7 @@ __device__ __forceinline__ void fine_axis(double x, const VolDev& V, double& t, 
     if (x < 0.0) x = x + box;
     if (x >= box) x = x - box;
     // x / h, correctly rounded; for h = 2^k the product with 2^-k is exact
-    t = V.h_pow2 ? x * V.inv_h : x / V.h;
+    t = V.h_pow2 ? x * V.inv_h : quotient_rn(x, V.h, V.inv_h);
     int qq = (int)floor(t);
     if (qq > M - 1) qq = M - 1;
     if (qq < 0) qq = 0;

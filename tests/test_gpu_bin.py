@@ -61,6 +61,25 @@ def test_bin_geometry_variants(sub_bits, n_cells, chunk):
     _compare(plan, vols)
 
 
+def test_bin_positions_next_to_fine_cell_faces():
+    # box 23 with 5 cells of 64 fine cells: h = 23/320 is not a power of two,
+    # so the fine cell and the offset come from the corrected binary64
+    # quotient x / h.  Positions within three ulps of the faces k h (and a
+    # few below 0, folded) are where a quotient off by one ulp would change
+    # the cell or the offset.
+    L, n_c, b = 23.0, 5, 6
+    h = L / (n_c << b)
+    rng = np.random.default_rng(31)
+    pos = rng.integers(0, n_c << b, (4000, 3)) * h
+    steps = rng.integers(-3, 4, pos.shape)
+    for s in range(3):
+        pos = np.where(steps > s, np.nextafter(pos, np.inf), pos)
+        pos = np.where(steps < -s, np.nextafter(pos, -np.inf), pos)
+    vols = [(pos, L)]
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), sub_bits=b, n_cells=[n_c])
+    _compare(plan, vols)
+
+
 def test_bin_edge_positions():
     L = 16.0
     pos = gen.uniform_box(500, L, 3)

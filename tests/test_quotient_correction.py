@@ -1,0 +1,69 @@
+"""The binning kernel's binary64 quotient for cell spacings h that are not
+powers of two: Markstein's fused multiply-add correction from y = RN(1/h),
+
+    q0 = x y,  q1 = fma(fma(-q0, h, x), y, q0),  t = fma(fma(-q1, h, x), y, q1),
+
+emulated here in exact rationals (each fused multiply-add rounds the exact
+value once), must equal the IEEE binary64 division x / h.  The theorem's
+premises are checked as well: q1 within one ulp of x / h and the last
+residual exact.  Inputs cover random positions, quotients below 1 and
+positions a few ulps either side of the faces k h, where a wrong rounding
+would change the fine cell."""
+import math
+from fractions import Fraction as Fr
+
+import numpy as np
+
+
+def _fma(a, b, c):
+    return float(Fr(a) * Fr(b) + Fr(c))      # float(Fraction) rounds to nearest even
+
+
+def _cases(rng, box, M):
+    h = box / M
+    xs = list(rng.uniform(0, box, 400)) + list(rng.uniform(0, h, 40))
+    for k in rng.integers(0, M, 150):
+        x = float(k) * h
+        for d in (-2, -1, 1, 2):
+            y = x
+            for _ in range(abs(d)):
+                y = float(np.nextafter(y, np.inf if d > 0 else -np.inf))
+            if 0 < y < box:
+                xs.append(y)
+    return h, [float(x) for x in xs if x >= 2.0 ** -900]
+
+
+def test_corrected_quotient_equals_ieee_division():
+    rng = np.random.default_rng(2024)
+    boxes = [23.0, 98.0, 17.0, 30.0, 1000.0 / 3.0, 0.7, 3.3e5] + list(rng.uniform(6.0, 600.0, 5))
+    n = 0
+    for box in boxes:
+        for M in (max(1, int(box // 4)) << 6, 13, 1000):
+            h, xs = _cases(rng, box, M)
+            y = float(1 / Fr(h))
+            for x in xs:
+                q = Fr(x) / Fr(h)
+                q0 = x * y
+                q1 = _fma(_fma(-q0, h, x), y, q0)
+                assert abs(Fr(q1) - q) < Fr(math.ulp(float(q))) or q == 0
+                r = Fr(x) - Fr(q1) * Fr(h)
+                assert Fr(float(r)) == r, "last residual not exact"
+                assert _fma(float(r), y, q1) == x / h, (box, M, x)
+                n += 1
+    assert n > 20000
+
+
+def test_single_correction_is_not_enough():
+    # the product x y alone can miss the one-ulp premise, so the first
+    # correction step is needed: box 23 in 13 cells (r_c = 1.5, no sub-cell
+    # bits), where RN(1/h) is 0.41 ulp from 1/h (rounding allows 0.5)
+    rng = np.random.default_rng(5)
+    h = 23.0 / 13
+    y = float(1 / Fr(h))
+    far = 0
+    for x in rng.uniform(0, 23.0, 4000):
+        x = float(x)
+        q = Fr(x) / Fr(h)
+        if abs(Fr(x * y) - q) >= Fr(math.ulp(float(q))):
+            far += 1
+    assert far > 0
