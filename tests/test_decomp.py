@@ -147,9 +147,10 @@ def _migrate_worker(rank, world, port, q):
         n = len(pos)
         ids = torch.arange(n, dtype=torch.int64)
         vel = torch.from_numpy(np.random.default_rng(9).normal(size=(n, 4)).astype(np.float32))
+        lab = torch.from_numpy(np.random.default_rng(10).integers(-5, 1000, n).astype(np.int32))
         s = Slabs(box, n_c, 1, world)
         mine = s.owned(pos, rank)
-        p, i, v = pos[mine], ids[mine], vel[mine]
+        p, i, v, lb = pos[mine], ids[mine], vel[mine], lab[mine]
         ok, moved = True, 0
         for step in range(4):
             # the same displacement field on every rank (drawn for all ids),
@@ -159,9 +160,10 @@ def _migrate_worker(rank, world, port, q):
             p = torch.remainder(p + disp[i], box)
             pos = torch.remainder(pos + disp, box)
             moved += int((s.owner(p) != rank).sum())
-            p, i, v = s.migrate(p, i, v)
+            p, i, v, lb = s.migrate(p, i, v, lb)          # a (n, 4) and a (n,) field travel along
             want = s.owned(pos, rank)
             ok &= torch.equal(i, ids[want]) and torch.equal(p, pos[want]) and torch.equal(v, vel[want])
+            ok &= lb.dtype == torch.int32 and torch.equal(lb, lab[want])
             got = s.exchange(p, i)
             ok &= all(torch.equal(a, b) for a, b in zip(got, s.local_set(pos, ids, rank)))
         q.put((rank, bool(ok), len(i), moved))
