@@ -56,11 +56,42 @@ __device__ __forceinline__ int volume_of_cell(int cell, const int* __restrict__ 
 // binary64 rate makes that the cost of binning when h is not a power of
 // two.  Below 2^-900 the residual could leave the normal range, so the
 // division is taken there (x = 0 included).
-__device__ __forceinline__ double quotient_rn(double x, double h, double y) {
-    if (x < 0x1p-900) return x / h;
+__device__ __forceinline__ double quotient_rn_normal(double x, double h, double y) {   // x >= 2^-900
     double q = x * y;
     q = fma(fma(-q, h, x), y, q);
     return fma(fma(-q, h, x), y, q);
+}
+
+__device__ __forceinline__ double quotient_rn(double x, double h, double y) {
+    return x < 0x1p-900 ? x / h : quotient_rn_normal(x, h, y);
+}
+
+// The integer form of the binary64 steps for a spacing h that is not a
+// power of two, as fine_axis_bits does for 2^-s: x in [0, box) checked on
+// its bit pattern (x below 2^-900, x = 0 included, is left to the binary64
+// code), t = x / h from quotient_rn, then floor(t) and t = mant 2^-F read
+// off t's bits.  q is floor(t) before the clamp to M - 1 (t can round up to
+// M for x just below box): the caller clamps the cell index, while the
+// offset is taken from the unclamped t.  Returns false where the caller
+// takes the binary64 code.
+__device__ __forceinline__ bool fine_axis_quot(double x, unsigned long long ubox, double h, double y, int& q,
+                                               unsigned long long& mant, int& F) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if (u >= ubox || u < (123ull << 52)) return false;       // outside [2^-900, box)
+    const double t = quotient_rn_normal(x, h, y);
+    const unsigned long long ut = (unsigned long long)__double_as_longlong(t);
+    const int E = (int)(ut >> 52) - 1023;                     // t >= 0: sign bit clear
+    if (E < 0) {                                              // t < 1 (zero or subnormal included)
+        q = 0;
+        mant = 0ull;
+        F = -1;
+        return true;
+    }
+    if (E > 52) return false;
+    mant = (ut & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    F = 52 - E;
+    q = (int)(mant >> F);
+    return true;
 }
 
 // Fine-grid coordinate of one axis; flags non-finite / out-of-range input.
@@ -93,13 +124,21 @@ __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, in
     bool bad = false;
     int q[3];
     const double x3[3] = {pos[3ll * i], pos[3ll * i + 1], pos[3ll * i + 2]};
-    bool fast = V.h_pow2 != 0;
-    if (fast) {
+    bool fast = true;
+    {
         const unsigned long long ubox = (unsigned long long)__double_as_longlong(V.box);
         unsigned long long mant;
         int F;
+        if (V.h_pow2) {
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) fast = fast && fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[ax], mant, F);
+            for (int ax = 0; ax < 3; ++ax) fast = fast && fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[ax], mant, F);
+        } else {
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                fast = fast && fine_axis_quot(x3[ax], ubox, V.h, V.inv_h, q[ax], mant, F);
+                q[ax] = min(q[ax], V.M - 1);
+            }
+        }
     }
     if (!fast) {
         double t[3];
@@ -174,11 +213,14 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
             if (valid[s]) {
                 orig[s] = perm[cell_start[cell] + rank];
                 const double x3[3] = {pos[3ll * orig[s]], pos[3ll * orig[s] + 1], pos[3ll * orig[s] + 2]};
-                // the integer path needs t >= 1 on every axis for the offsets
-                bool f = V.h_pow2 != 0;
+                // the integer path needs t >= 1 on every axis for the offsets;
+                // q holds the unclamped floor(t) there (the anchor is clamped)
+                bool f = true;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax)
-                    f = f && fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[s][ax], mant[s][ax], F[s][ax]) &&
+                    f = f && (V.h_pow2 ? fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[s][ax], mant[s][ax], F[s][ax])
+                                       : fine_axis_quot(x3[ax], ubox, V.h, V.inv_h, q[s][ax], mant[s][ax],
+                                                        F[s][ax])) &&
                         F[s][ax] >= 0;
                 fast[s] = f;
                 if (!f) {
@@ -192,7 +234,7 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
         float bl[3], bh[3];
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            qa[ax] = __shfl_sync(kFull, q[0][ax], 0);      // slot 0 (rank r0) always exists
+            qa[ax] = min(__shfl_sync(kFull, q[0][ax], 0), V.M - 1);   // slot 0 (rank r0) always exists
             bl[ax] = __int_as_float(0x7f800000);          // +inf
             bh[ax] = __int_as_float(0xff800000);          // -inf
         }

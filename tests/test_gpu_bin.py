@@ -75,6 +75,12 @@ def test_bin_positions_next_to_fine_cell_faces():
     for s in range(3):
         pos = np.where(steps > s, np.nextafter(pos, np.inf), pos)
         pos = np.where(steps < -s, np.nextafter(pos, -np.inf), pos)
+    # one to three ulps below the box side, where x / h can round up to M
+    # (cell index clamped to M - 1, offset taken from the unclamped quotient)
+    top = [L]
+    for _ in range(3):
+        top.append(float(np.nextafter(top[-1], -np.inf)))
+    pos[:60] = np.array(top[1:])[rng.integers(0, 3, (60, 3))]
     vols = [(pos, L)]
     plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), sub_bits=b, n_cells=[n_c])
     _compare(plan, vols)
