@@ -31,7 +31,10 @@ def _plans(plan, steps: int):
     """A tuple of one shared plan, or of one plan per substep."""
     if isinstance(plan, Plan):
         return (plan,)
-    plans = tuple(plan)
+    try:
+        plans = tuple(plan)
+    except TypeError:
+        plans = ()
     if len(plans) != steps or not all(isinstance(p, Plan) for p in plans):
         raise ValueError("give one Plan, or a sequence of one Plan per substep")
     return plans

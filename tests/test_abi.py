@@ -140,3 +140,14 @@ def test_fof_argument_checks_need_no_device(lib):
     assert lib.sr_fof_set_iteration_limit(None, 5) == 1
     lib.sr_fof_destroy.restype = ctypes.c_int
     assert lib.sr_fof_destroy(None) == 0
+
+
+def test_trajectory_plan_list_checks_need_no_device():
+    # one plan per substep: the list must hold exactly `steps` plans
+    from paper_1411_3396_b300.autograd import _plans
+    with pytest.raises(ValueError):
+        _plans([object(), object()], 2)
+    with pytest.raises(ValueError):
+        _plans([], 3)
+    with pytest.raises(ValueError):
+        _plans(None, 1)
