@@ -275,9 +275,15 @@ int sr_invariants(sr_plan* plan, int64_t n, const float* vel, const float* acc, 
  * that may neither allocate nor synchronise).
  * Scratch: a fixed 224 KiB device array inside the library (one per device
  * that loads it, held until the process exits), enough for n up to
- * 67,108,864 rows; larger n fails with SR_ERR_CAPACITY.  The first call on
- * each device looks up that array's device address (a CUDA runtime query),
- * so make the first call on a device before any stream capture.  All calls
+ * 67,108,864 rows; larger n fails with SR_ERR_CAPACITY.  The first call in
+ * each CUDA context looks up that array's device address (a CUDA runtime
+ * query; a context made after a device reset gets its own lookup), so make
+ * the first call on a device before any stream capture.  Under CUDA's lazy
+ * module loading (the default) that first call is also what loads this
+ * library's device code on the device, and the load allocates the array and
+ * the code there: callers whose allocator must own all device memory from
+ * some point on should warm the entry point up before it, for example with
+ * n = 0 (which writes seven zeros to out).  Later calls allocate nothing.  All calls
  * share the array: calls whose kernels overlap on the GPU (different
  * streams, no ordering between them) race and may return wrong sums; calls
  * on one stream are safe.  Every call rewrites all partial sums it reads.

@@ -37,6 +37,10 @@ def _plans(plan, steps: int):
         plans = ()
     if len(plans) != steps or not all(isinstance(p, Plan) for p in plans):
         raise ValueError("give one Plan, or a sequence of one Plan per substep")
+    if len(plans) > 1 and len({id(p) for p in plans}) != len(plans):
+        # a plan listed twice would hold only its last substep's binning when
+        # the backward pass reads it for an earlier one
+        raise ValueError("the per-substep plans must be distinct objects; give one Plan to share it")
     return plans
 
 

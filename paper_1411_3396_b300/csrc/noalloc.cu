@@ -28,24 +28,66 @@ constexpr long long kNaMaxRows = kNaRowsPerBlock * kNaMaxBlocks;   // 67,108,864
 static __device__ __align__(256) double g_na_partials[kNaMaxBlocks * 7];
 
 std::mutex g_na_mutex;
-std::unordered_map<int, double*> g_na_addr;          // device -> address of g_na_partials
+std::unordered_map<unsigned long long, double*> g_na_addr;   // context id -> address of g_na_partials
 
-// Device address of g_na_partials on the current device, looked up once per
-// device (the symbol name is only a host-side handle, not a device address).
+// Driver calls reached through the runtime's entry-point query, so the
+// library needs no link-time dependency on the driver library.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+// Process-unique id of the current CUDA context (cuCtxGetId: ids are never
+// reused, unlike context handles and device ordinals).  Called with
+// g_na_mutex held.
+int na_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+            return set_error(SR_ERR_CUDA, "driver entry point cuCtxGetCurrent not found");
+        void* g = nullptr;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !g)
+            return set_error(SR_ERR_CUDA, "driver entry point cuCtxGetId not found");
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        get_id = reinterpret_cast<CtxGetIdFn>(g);
+    }
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0) return set_error(SR_ERR_CUDA, "cuCtxGetCurrent failed");
+    if (!ctx) {
+        // no context bound to this thread yet: bind the current device's
+        // primary context, as the runtime's first call would
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+        if (get_current(&ctx) != 0 || !ctx) return set_error(SR_ERR_CUDA, "no current CUDA context");
+    }
+    if (get_id(ctx, id) != 0) return set_error(SR_ERR_CUDA, "cuCtxGetId failed");
+    return SR_OK;
+}
+
+// Device address of g_na_partials in the current context, looked up once
+// per context (the symbol name is only a host-side handle, not a device
+// address).  Keyed by the context's id, so a device reset, which makes a new
+// context, also makes a new lookup instead of reusing a stale address.
 int na_scratch(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    auto it = g_na_addr.find(dev);
+    unsigned long long id = 0;
+    const int rc = na_context_id(&id);
+    if (rc) return rc;
+    auto it = g_na_addr.find(id);
     if (it != g_na_addr.end()) {
         *out = it->second;
         return SR_OK;
     }
     void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_na_partials);
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_na_partials);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_na_partials)");
-    g_na_addr[dev] = static_cast<double*>(ptr);
+    g_na_addr[id] = static_cast<double*>(ptr);
     *out = static_cast<double*>(ptr);
     return SR_OK;
 }

@@ -151,3 +151,12 @@ def test_trajectory_plan_list_checks_need_no_device():
         _plans([], 3)
     with pytest.raises(ValueError):
         _plans(None, 1)
+    # the same plan object twice would keep only its last substep's binning
+    from paper_1411_3396_b300.api import Plan
+    p, q = Plan.__new__(Plan), Plan.__new__(Plan)
+    with pytest.raises(ValueError):
+        _plans([p] * 3, 3)
+    with pytest.raises(ValueError):
+        _plans([p, q, p], 3)
+    assert _plans([p, q], 2) == (p, q)
+    assert _plans(p, 5) == (p,)

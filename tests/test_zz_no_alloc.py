@@ -61,6 +61,22 @@ def test_noalloc_invariants_null_inputs_and_limits():
     vv = v.cpu().numpy().astype(np.float64)
     np.testing.assert_allclose(o[0:3], vv[:, :3].sum(axis=0), rtol=1e-12, atol=1e-10)
     assert np.all(o[3:6] == 0.0)
+    ke = 0.5 * np.sum(vv[:, :3] * vv[:, :3])
+    np.testing.assert_allclose(o[6], ke, rtol=1e-12)
+    # no velocities: only the acceleration sums are nonzero
+    _, a = _rows(1000, 4)
+    out.fill_(float("nan"))
+    rc = lib.sr_invariants_noalloc(1000, None, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   _stream())
+    assert rc == 0
+    o = out.cpu().numpy()
+    aa = a.cpu().numpy().astype(np.float64)
+    assert np.all(o[0:3] == 0.0) and o[6] == 0.0
+    np.testing.assert_allclose(o[3:6], aa[:, :3].sum(axis=0), rtol=1e-12, atol=1e-10)
+    # n = 0, the warm-up call: seven zeros
+    out.fill_(float("nan"))
+    assert lib.sr_invariants_noalloc(0, None, None, ctypes.c_void_p(out.data_ptr()), _stream()) == 0
+    assert np.all(out.cpu().numpy() == 0.0)
     # beyond the static scratch: rejected before any launch
     assert lib.sr_invariants_noalloc(67_108_865, None, None, ctypes.c_void_p(out.data_ptr()), _stream()) == 3
     assert b"static scratch" in lib.sr_last_error()
