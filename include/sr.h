@@ -330,16 +330,32 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  *   7:    as 2, with split partial sums;
  *   8..11: packed two-wide binary32 pair loop (split partial sums,
  *         batches of 128 neighbours), launch shapes as 1, 2, 4, 3;
- *   12:   the packed loop in batches of 64, launch shape as 3.
+ *   12:   the packed loop in batches of 64, launch shape as 3;
+ *   13, 14: variants 11 and 12 with the neighbour chunks enumerated for
+ *         all cells at once (one lane per cell, then one lane per candidate
+ *         chunk) and the next chunk's slots loaded during the current one:
+ *         the same chunks in the same order, bit-identical to 11 and 12;
+ *   15, 16: grouped kernel for low density: each chunk's 32 slots form
+ *         i-groups of G consecutive slots (15: G = 8, 16: G = 16), each
+ *         with a neighbour ring culled against its own box, evaluated by
+ *         all 32 lanes (32 / G lanes per slot, packed loop, group batches
+ *         of 96); 256-thread blocks, 3 per SM.
  * Variants 0..6 are bit-identical (batches of 32 neighbours); so are 8..11
- * (packed, batches of 128).  Split partial sums add even and odd neighbours
+ * and 13 (packed, batches of 128), and 12 and 14.  Split partial sums add even and odd neighbours
  * of a batch separately before the compensated update; variant 7 does so
  * over batches of 32 and variant 12 over batches of 64.  Variants of
- * different groups differ in the last bits.
+ * different groups differ in the last bits.  All variants evaluate the same
+ * binary32 pair terms and count the same pairs.
  * Plans with 64-particle chunks support variants 0..3.
+ * The counting mode of sr_force (pair_count or per_particle given) runs the
+ * grouped kernel when a grouped variant is selected, else one fixed
+ * variant-0-order kernel.
  * Errors: SR_ERR_ARG (out of range or not available for the chunk size).
  */
 int sr_plan_set_variant(sr_plan* plan, int variant);
+
+/* sr_variant_count -- the number of pair-kernel variants (17: 0..16). */
+int sr_variant_count(void);
 
 /*
  * sr_autotune -- time each pair-kernel variant on the data of the last
@@ -347,9 +363,9 @@ int sr_plan_set_variant(sr_plan* plan, int variant);
  * keep the fastest.  When the second fastest is within 3% of it, the two
  * are timed again, one launch of each in turn over 2 reps + 1 rounds, and
  * the faster total is kept.  acc: device float4 rows used as scratch output.
- * ms_out: host float[13], nullable, receives the mean time per variant
- * of the first pass (0 for variants not available for the plan's chunk
- * size).
+ * ms_out: host float[sr_variant_count()], nullable, receives the mean time
+ * per variant of the first pass (0 for variants not available for the
+ * plan's chunk size).
  * This is a set-up call: it synchronises and must not be captured.
  * Errors: SR_ERR_STATE before the first sr_bin, SR_ERR_ARG, SR_ERR_CUDA.
  */

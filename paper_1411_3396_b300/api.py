@@ -202,7 +202,7 @@ class Plan:
         fastest and returns the per-variant mean times (ms)."""
         n = self._need_binned()
         acc = torch.empty((n, 4), dtype=torch.float32, device="cuda")
-        ms = (ctypes.c_float * 13)()
+        ms = (ctypes.c_float * load().sr_variant_count())()
         check(load().sr_autotune(self._h, _ptr(acc), int(reps), ms, _stream()))
         return list(ms)
 

@@ -501,6 +501,8 @@ int sr_plan_set_variant(sr_plan* p, int variant) {
     return SR_OK;
 }
 
+int sr_variant_count(void) { return kVariants; }
+
 int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!p->binned) return set_error(SR_ERR_STATE, "sr_autotune before sr_bin");

@@ -100,7 +100,9 @@ constexpr int kScanThreads = 256;
 constexpr int kScanTile = kScanItems * kScanThreads;
 constexpr int kRadixBits = 8;
 constexpr int kRadixBuckets = 1 << kRadixBits;
-constexpr int kVariants = 13;       // force-kernel variants (launch shape / accumulation)
+constexpr int kGroupedFirst = 15;   // force-kernel variants 0..14: one 32-lane i-group per chunk
+constexpr int kGroupedVariants = 2; // 15, 16: several smaller i-groups per chunk (force_grp.cu)
+constexpr int kVariants = kGroupedFirst + kGroupedVariants;
 
 // Per-volume constants, device resident, read once per work item.
 // Lengths inside kernels are in units of the fine grid h = L / (n_c 2^b).
@@ -211,6 +213,7 @@ struct sr_plan {
     int force_blocks_v[sr::kVariants] = {};
     int vjp_blocks = 0;
     int count_blocks = 0;
+    int grp_count_blocks[sr::kGroupedVariants] = {};   // counting mode of the grouped variants
     int warps_per_block = 8;               // of the selected force variant
 };
 
@@ -256,6 +259,10 @@ int launch_force(sr_plan* p, float* acc, unsigned long long* pairs, int* per_par
 int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int accumulate,
                cudaStream_t st);
 int force_occupancy(sr_plan* p);
+// grouped pair kernel (force_grp.cu), 32-particle chunks only
+int grouped_occupancy(sr_plan* p, int* blocks, int* count_blocks);
+int launch_force_grouped(sr_plan* p, float* acc, unsigned long long* pairs, int* per_particle,
+                         cudaStream_t st, float* vel, float kdt);
 
 // plain kernel (plain.cu)
 int launch_force_plain(sr_plan* p, float* acc, cudaStream_t st);

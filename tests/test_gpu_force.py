@@ -110,7 +110,64 @@ def test_all_kernel_variants_give_identical_forces(small_case):
             assert_force_close(acc, a_ref, f"{name} variant {v}")
         assert acc.tobytes() == packed.tobytes(), f"variant {v}"
     plan.set_variant(12)                      # the packed loop in batches of 64
-    assert_force_close(to_np(plan.force()), a_ref, f"{name} variant 12")
+    acc12 = to_np(plan.force())
+    assert_force_close(acc12, a_ref, f"{name} variant 12")
+    # the flat neighbour enumeration visits the same chunks in the same
+    # order: 13 gives 11's bits, 14 gives 12's
+    plan.set_variant(13)
+    assert to_np(plan.force()).tobytes() == packed.tobytes(), "variant 13"
+    plan.set_variant(14)
+    assert to_np(plan.force()).tobytes() == acc12.tobytes(), "variant 14"
+
+
+GROUPED = range(15, 17)        # i-groups of 8 or 16 slots, each with its own ring
+
+
+def test_grouped_variants_forces_and_counts(small_case):
+    # the grouped kernel: forces within the oracle bar, per-particle pair
+    # counts bit-exact (same binary32 predicate as the 32-lane kernel), and
+    # its counting mode gives the force mode's bits
+    from paper_1411_3396_b300 import SrError
+    name, w, chunk = small_case
+    pos = np.concatenate([p for p, _ in w["volumes"]])
+    plan = make_plan(w["volumes"], w["params"], chunk_size=chunk)
+    plan.bin(torch.from_numpy(pos).cuda())
+    if chunk == 64:
+        for v in GROUPED:
+            with pytest.raises(SrError):
+                plan.set_variant(v)
+        return
+    B = oracle_binning(plan, w["volumes"])
+    ref = oforce.pair_counts_fp32(B, w["volumes"], w["params"]["rc"], w["params"]["eps"])
+    a_ref, _ = oracle_force(w["volumes"], w["params"])
+    for v in GROUPED:
+        plan.set_variant(v)
+        acc_c, pairs, pp = plan.force(count=True, per_particle=True)
+        np.testing.assert_array_equal(to_np(pp), ref, err_msg=f"variant {v}")
+        assert int(pairs.item()) == int(ref.sum()), f"variant {v}"
+        acc = to_np(plan.force())
+        assert acc.tobytes() == to_np(acc_c).tobytes(), f"variant {v}"
+        assert_force_close(acc, a_ref, f"{name} variant {v}")
+        assert np.all(acc[:, 3] == 0)
+        again = to_np(plan.force())
+        assert again.tobytes() == acc.tobytes(), f"variant {v} not deterministic"
+
+
+def test_grouped_variants_brute_force_tiny_boxes():
+    # boxes of 2 to 4 cells per axis: chunks see their own images through
+    # several faces, ragged groups in nearly every chunk
+    for L, n, seed in [(7.0, 300, 1), (8.0, 512, 2), (10.0, 400, 3), (6.5, 64, 4), (9.0, 37, 5)]:
+        pos = gen.uniform_box(n, L, seed)
+        params = dict(rc=3.0, eps=0.1, sigma=0.8)
+        c = ofit.fit_poly(3.0, 0.8, 0.1)
+        a_ref, cnt = oforce.accel_brute(pos, L, 3.0, 0.1, c)
+        plan = make_plan([(pos, L)], params)
+        plan.bin(torch.from_numpy(pos).cuda())
+        for v in GROUPED:
+            plan.set_variant(v)
+            acc, pairs, pp = plan.force(count=True, per_particle=True)
+            assert_force_close(to_np(acc), a_ref, f"L={L} variant {v}")
+            assert abs(int(pairs.item()) - int(cnt.sum())) <= 8
 
 
 def test_plain_kernel_matches_oracle(small_case):

@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("chunk", [32, 64])
-def test_force_kick_equals_force_then_kick(chunk):
+@pytest.mark.parametrize("chunk,variant", [(32, None), (64, None), (32, 14), (32, 15), (32, 16)])
+def test_force_kick_equals_force_then_kick(chunk, variant):
     from paper_1411_3396_b300 import kick
     w = wc.make_workload(wc.small_variant("clustered256"))
     (pos, box), = w["volumes"]
@@ -25,6 +25,8 @@ def test_force_kick_equals_force_then_kick(chunk):
     v0[:, :3] = torch.from_numpy(w["velocities"]).float()
     plan = make_plan(w["volumes"], w["params"], chunk_size=chunk)
     plan.bin(torch.from_numpy(pos).cuda())
+    if variant is not None:                   # the grouped kernel's epilogue
+        plan.set_variant(variant)
     a1 = plan.force()
     v1 = v0.clone()
     kick(a1, v1, 0.01)

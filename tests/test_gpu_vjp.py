@@ -159,6 +159,46 @@ def test_trajectory_full_size_64cubed():
             (np.median(rel), norm, rel.max())
 
 
+def test_vjp_per_substep_on_gpu_states_64cubed():
+    # separates the VJP kernel's own error from trajectory divergence at full
+    # size: each substep's GPU VJP is compared, at the force bar, with the
+    # oracle's VJP at the GPU's own state x_k and the GPU's own cotangent
+    # (the binary32 dt * vbar the kernel applies); the end-to-end bar of
+    # test_trajectory_full_size_64cubed covers the whole trajectory
+    from paper_1411_3396_b300 import Plan, kick
+    cfg = wc.CONFIGS["diff64"]
+    box, n_side, steps, dt = cfg["box"], cfg["n_side"], cfg["steps"], cfg["dt"]
+    rc, eps, sigma = cfg["rc"], cfg["eps"], cfg["sigma"]
+    x0, v0, xt = _diff_setup(n_side, box)
+    n = len(x0)
+    plan = Plan(box, rc, eps, sigma, n)
+    x = torch.from_numpy(x0).cuda()
+    v = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    v[:, :3] = torch.from_numpy(v0).float()
+    acc = torch.empty_like(v)
+    states = []
+    for _ in range(steps):                   # the forward substeps, checkpointing x_k
+        states.append(x.clone())
+        plan.bin(x)
+        plan.force(acc)
+        kick(acc, v, dt)
+        plan.drift(x, v, dt)
+    d = x - torch.from_numpy(xt).cuda()
+    d = d - box * torch.round(d / box)
+    xbar = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    xbar[:, :3] = (2.0 * d).float()
+    vbar = torch.zeros_like(xbar)
+    c = ofit.fit_poly(rc, sigma, eps)
+    for k in range(steps - 1, -1, -1):       # the reverse sweep, one substep at a time
+        kick(xbar, vbar, dt)                 # vbar += dt * xbar
+        plan.bin(states[k])
+        out = plan.vjp(vbar, g_scale=dt)
+        g = (to_np(vbar)[:, :3] * np.float32(dt)).astype(np.float64)
+        ref = oint.force_vjp(to_np(states[k]), box, rc, eps, c, g)
+        assert_force_close(to_np(out), ref, f"vjp of substep {k}")
+        xbar += out
+
+
 def test_trajectory_graph_is_bit_identical_to_eager():
     # the captured forward + loss + gradient sweep replays the eager kernels
     from paper_1411_3396_b300 import TrajectoryGraph, trajectory
