@@ -134,7 +134,7 @@ def measured_peaks():
     return {}
 
 
-def kernel_source_hash(names=("force.cu", "sr_internal.h")):
+def kernel_source_hash(names=("force.cu", "pairs.cuh", "sr_internal.h")):
     h = hashlib.sha1()
     for name in names:
         with open(os.path.join(ROOT, "paper_1411_3396_b300", "csrc", name), "rb") as f:
@@ -175,7 +175,7 @@ def time_hbm_kernels(plan, x, acc, vel, n, hbm_gbs, reps=5):
     return out
 
 
-def recorded_traffic(note=PROFILE_NOTE, names=("force.cu", "sr_internal.h")):
+def recorded_traffic(note=PROFILE_NOTE, names=("force.cu", "pairs.cuh", "sr_internal.h")):
     """DRAM bytes per launch of a kernel from its committed ncu summary, or
     None if the summary is missing or was taken on a different kernel source."""
     if not os.path.exists(note):
@@ -256,6 +256,20 @@ def shard_volumes(sizes, world, rank):
     return [v for v in range(len(sizes)) if owner[v] == rank]
 
 
+def slab_step(slabs, x_own, ids_own, acc_local, vel_local, force_kick, group=None):
+    """One step of the overload slab decomposition (Sec. 2, Sec. 2.1) on
+    this rank: the ghost exchange (this rank's owned particles, in id
+    order, first; then the particles of the neighbouring slabs' edge
+    cells), then force_kick(x_local, owned, acc_rows, vel_rows) on the local
+    set, which bins the ghosts as passive and writes and kicks the owned
+    rows only.  The owned rows are the first len(x_own) rows of acc_local
+    and vel_local.  Returns the local set's size."""
+    xl, _, own = slabs.exchange(x_own, ids_own, group=group)
+    m = len(xl)
+    force_kick(xl, own, acc_local[:m], vel_local[:m])
+    return m
+
+
 def reduce_over_ranks(pairs, ms, world, device):
     """Whole-job pairs (sum over ranks) and step time (max over ranks)."""
     if world == 1:
@@ -270,8 +284,9 @@ def reduce_over_ranks(pairs, ms, world, device):
 
 
 def make_inputs(name, n_particles=0, world=1, rank=0):
-    """Volumes this rank evaluates: single-volume workloads are replicated
-    on every rank; a batch is sharded across ranks."""
+    """Volumes this rank evaluates: a batch is sharded across ranks; a single
+    volume is returned whole on every rank (each rank then keeps its slab,
+    run_ours)."""
     from workloads import configs as wc
     cfg = wc.resized(name, n_particles) if n_particles else wc.CONFIGS[name]
     w = wc.make_workload(cfg)
@@ -406,8 +421,37 @@ def run_ours(args, rank, world, local_rank):
                     chunk_size=args.chunk_size)
     dt = prm["dt"]
     graph_stream = torch.cuda.Stream() if batch else None
+    slabbed = world > 1 and not batch
+    if slabbed:
+        # overload slab decomposition of the one volume: every rank keeps the
+        # particles of its slab of cells (in id order) and, each step,
+        # receives the ghosts of the neighbouring slabs' edge cells, binned
+        # as passive (forced only as neighbours)
+        from paper_1411_3396_b300.decomp import Slabs
+        slabs = Slabs.of_plan(plan, world)
+        mine = slabs.owned(x, rank)
+        x_own = x[mine].contiguous()
+        ids_own = torch.arange(n, device=dev)[mine].contiguous()
+        n_own = len(x_own)
+        vel_loc = torch.zeros_like(vel)
+        vel_loc[:n_own] = vel[mine]
+        acc_loc = torch.zeros_like(acc)
+        slab_ev = [None]
+
+        def slab_force_kick(xl, own, a, v):
+            plan.bin(xl, active=own)
+            if slab_ev[0] is not None:
+                slab_ev[0][0].record()
+            plan.force_kick(a, v, dt)
+            if slab_ev[0] is not None:
+                slab_ev[0][1].record()
 
     def step(ev=None):
+        if slabbed:
+            slab_ev[0] = ev
+            slab_step(slabs, x_own, ids_own, acc_loc, vel_loc, slab_force_kick)
+            plan.invariants(vel_loc[:n_own], acc_loc[:n_own], inv)
+            return
         if batch:
             # one captured graph: bin + persistent force + kick over all volumes
             if ev is not None:
@@ -425,13 +469,17 @@ def run_ours(args, rank, world, local_rank):
         plan.invariants(vel, acc, inv)
 
     # pair count of this configuration (binary32 predicate, counting variant)
-    plan.bin(x)
+    if slabbed:
+        xl, _, own = slabs.exchange(x_own, ids_own)
+        plan.bin(xl, active=own)
+    else:
+        plan.bin(x)
     tune_ms = None
     if args.variant >= 0:
         plan.set_variant(args.variant)
     elif not args.no_autotune:
         tune_ms = plan.autotune(reps=1)
-    _, pairs_t, _ = plan.force(acc, count=True)
+    _, pairs_t, _ = plan.force(acc_loc[:len(xl)] if slabbed else acc, count=True)   # slabs: owned rows' pairs
     torch.cuda.synchronize()
     pairs = int(pairs_t.item())
     info = plan.info()
@@ -488,7 +536,7 @@ def run_ours(args, rank, world, local_rank):
 
     # plain one-launch-per-slab kernel on the same binned input
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and not slabbed:
         torch.cuda.set_stream(torch.cuda.default_stream())
         plan.bin(x)
         plan.force_plain(acc)
@@ -505,7 +553,7 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end: pinned host buffers, H2D + step + D2H inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not slabbed:
         torch.cuda.set_stream(torch.cuda.default_stream())
         pos_h = torch.from_numpy(pos).pin_memory()
         vel_h = vel.cpu().pin_memory()
@@ -530,7 +578,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = pairs * FLOPS_PER_PAIR / (force_ms * 1e-3) / 1e12
     # the recorded counters are for the full clustered 256^3 launch only
     traffic = recorded_traffic() if (args.workload == "clustered256" and not args.n_particles) else None
-    hbm_kernels = None if batch else time_hbm_kernels(plan, x, acc, vel, n, float(peaks.get("hbm_gbs", 6400.0)))
+    hbm_kernels = None if (batch or slabbed) else time_hbm_kernels(plan, x, acc, vel, n, float(peaks.get("hbm_gbs", 6400.0)))
 
     if rank != 0:
         return
@@ -549,7 +597,7 @@ def run_ours(args, rank, world, local_rank):
                    "in_range_fraction": pairs / max(evals, 1),
                    "lane_fill": evals / max(lane_evals, 1),
                    "l2": f"inputs larger than L2 ({n * 24 / 1e6:.0f} MB positions); no flush",
-                   "parallelism": (f"sharded{world}" if batch else f"replicas{world}") if world > 1 else "single"},
+                   "parallelism": (f"sharded{world}" if batch else f"slabs{world}") if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "k_pairs<force> (kick fused)", "kernel_ms": force_ms, "graph_ms": graph_ms,

@@ -57,14 +57,16 @@ extern "C" {
 #define SR_EXPORT_PERM              0  /* int32[n]: sorted position -> caller index */
 #define SR_EXPORT_CELL_START        1  /* int32[total_cells+1]: first sorted position of each cell */
 #define SR_EXPORT_CELL_CHUNK_START  2  /* int32[total_cells+1]: first chunk of each cell */
-#define SR_EXPORT_SLOT_POS          3  /* float[4*C*n_chunks]: chunk-relative offsets (units of h), C = chunk size */
+#define SR_EXPORT_SLOT_POS          3  /* float[4*C*n_chunks]: chunk-relative offsets (units of h), C = chunk size;
+                                              w = 1 active, -1 passive (sr_bin_active), 0 empty slot */
 #define SR_EXPORT_SLOT_IDX          4  /* int32[C*n_chunks]: caller index per slot, -1 = empty */
 #define SR_EXPORT_CHUNK_META        5  /* int32[4*n_chunks]: anchor (qx, qy, qz) and volume */
 #define SR_EXPORT_CHUNK_LO          6  /* float[4*n_chunks]: bbox min (x,y,z), w = particle count (int bits) */
-#define SR_EXPORT_CHUNK_HI          7  /* float[4*n_chunks]: bbox max (x,y,z), w = 0 */
+#define SR_EXPORT_CHUNK_HI          7  /* float[4*n_chunks]: bbox max (x,y,z), w = active particles (int bits) */
 #define SR_EXPORT_ORDER             8  /* int32[n_chunks]: work order of the persistent kernel */
 #define SR_EXPORT_COST              9  /* uint32[n_chunks]: estimated pair evaluations per chunk */
-#define SR_EXPORT_COUNTERS         10  /* int64[8]: n_chunks, queue head, error bits, ... */
+#define SR_EXPORT_COUNTERS         10  /* int64[8]: queue head, error bits, cost total, candidate evaluations
+                                              (valid i), evaluations x lanes, work items, 2 reserved */
 
 /* Physics and binning parameters of one periodic volume (lengths in the
  * same unit as the positions; the workloads use the mean inter-particle
@@ -165,6 +167,21 @@ int sr_plan_volume_info(const sr_plan* plan, int v, int64_t* n, double* box, int
  * sr_plan_status then returns SR_ERR_RANGE.
  */
 int sr_bin(sr_plan* plan, const double* pos, int64_t n, void* stream);
+
+/*
+ * sr_bin_active -- sr_bin with a mask of the particles whose forces are
+ * wanted (Sec. 2.1: a node evolves its active particles; the passive ones,
+ * the overload copies of its neighbours' particles, are read-only).
+ * active: device, n bytes in caller order, nonzero = active; NULL makes
+ * every particle active (sr_bin).  Every particle is binned and serves as a
+ * neighbour; the pair kernels (sr_force, sr_force_kick, sr_force_vjp and
+ * the counting mode) take as work items only the chunks that hold an active
+ * particle, and write only active particles' rows: the acc, vel, g_pos and
+ * per_particle rows of passive particles are left untouched, and
+ * pair_count adds the active particles' pairs only.  The mask is read
+ * during this call only.  Errors as sr_bin.
+ */
+int sr_bin_active(sr_plan* plan, const double* pos, const uint8_t* active, int64_t n, void* stream);
 
 /*
  * sr_force -- short-range accelerations of every binned particle (Sec. 2,

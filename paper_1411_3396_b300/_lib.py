@@ -71,6 +71,7 @@ SIGNATURES = {
     "sr_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
     "sr_plan_set_variant": (c_int, [c_void_p, c_int]),
     "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
+    "sr_bin_active": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "sr_variant_count": (c_int, []),
     "sr_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
     "sr_graph_launch": (c_int, [c_void_p, c_void_p]),

@@ -117,22 +117,38 @@ class Plan:
         return dict(n=n.value, box=box.value, n_cells=nc.value, h=h.value)
 
     # -- hot path ------------------------------------------------------------
-    def bin(self, pos: torch.Tensor):
+    def bin(self, pos: torch.Tensor, active: torch.Tensor | None = None):
+        """Bin pos (n, 3) binary64.  active: optional (n,) bool or uint8 mask
+        of the particles whose forces are wanted (sr_bin_active); the others
+        are neighbours only, and their output rows are left untouched."""
         _need(pos, torch.float64, 3, "pos")
-        check(load().sr_bin(self._h, _ptr(pos), pos.shape[0], _stream()))
+        if active is None:
+            check(load().sr_bin(self._h, _ptr(pos), pos.shape[0], _stream()))
+        else:
+            if active.dtype not in (torch.bool, torch.uint8) or active.shape != (pos.shape[0],) \
+                    or not active.is_cuda or not active.is_contiguous():
+                raise ValueError("active must be a contiguous CUDA bool/uint8 tensor of shape (n,)")
+            check(load().sr_bin_active(self._h, _ptr(pos), _ptr(active), pos.shape[0], _stream()))
         self.n = pos.shape[0]
         self.binnings += 1
         return self
 
-    def force(self, acc: torch.Tensor | None = None, count: bool = False, per_particle: bool = False):
+    def force(self, acc: torch.Tensor | None = None, count: bool = False, per_particle=False):
         """Accelerations (n, 4) float32; with count/per_particle also the
-        in-range pair total (uint64 device scalar) / per-particle counts."""
+        in-range pair total (uint64 device scalar) / per-particle counts
+        (per_particle: True, or an (n,) int32 CUDA tensor to write into)."""
         n = self._need_binned()
         if acc is None:
             acc = torch.empty((n, 4), dtype=torch.float32, device="cuda")
         _need(acc, torch.float32, 4, "acc", n)
         pairs = torch.zeros(1, dtype=torch.int64, device="cuda") if count else None
-        pp = torch.empty(n, dtype=torch.int32, device="cuda") if per_particle else None
+        if isinstance(per_particle, torch.Tensor):
+            if per_particle.dtype != torch.int32 or per_particle.shape != (n,) or not per_particle.is_cuda \
+                    or not per_particle.is_contiguous():
+                raise ValueError("per_particle must be a contiguous CUDA int32 tensor of shape (n,)")
+            pp = per_particle
+        else:
+            pp = torch.empty(n, dtype=torch.int32, device="cuda") if per_particle else None
         check(load().sr_force(self._h, _ptr(acc), _ptr(pairs), _ptr(pp), _stream()))
         if count or per_particle:
             return acc, pairs, pp

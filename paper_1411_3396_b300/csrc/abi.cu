@@ -331,18 +331,22 @@ int sr_plan_volume_info(const sr_plan* p, int v, int64_t* n, double* box, int* n
     return SR_OK;
 }
 
-int sr_bin(sr_plan* p, const double* pos, int64_t n, void* stream) {
+int sr_bin_active(sr_plan* p, const double* pos, const uint8_t* active, int64_t n, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
     if (!pos && n > 0) return set_error(SR_ERR_ARG, "pos is null");
     if (n < 0) return set_error(SR_ERR_ARG, "n must be >= 0");
     if (n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
     if (p->n_vol > 1 && n != p->capacity)
         return set_error(SR_ERR_CAPACITY, "a batch plan bins exactly the sum of its volume counts");
-    int rc = launch_bin(p, pos, n, as_stream(stream));
+    int rc = launch_bin(p, pos, n, as_stream(stream), active);
     if (rc) return rc;
     p->n_binned = n;
     p->binned = true;
     return SR_OK;
+}
+
+int sr_bin(sr_plan* p, const double* pos, int64_t n, void* stream) {
+    return sr_bin_active(p, pos, nullptr, n, stream);
 }
 
 int sr_force(sr_plan* p, float* acc, unsigned long long* pair_count, int* per_particle, void* stream) {

@@ -179,14 +179,17 @@ __global__ void __launch_bounds__(256) k_chunk_cell(const int* __restrict__ ccs,
 }
 
 // One warp per chunk of C = 32 K slots (lane l fills slots l + 32 s):
-// slot positions / indices, anchor, bounding box.
+// slot positions / indices, anchor, bounding box.  active (caller order,
+// nullable = every particle active) marks the particles whose forces are
+// wanted: slot w = 1 (active), -1 (passive, a neighbour only) or 0 (empty);
+// chunk_hi.w = the chunk's count of active particles (int bits).
 template <int K>
 __global__ void __launch_bounds__(256) k_chunk_fill(
     const double* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ cell_start,
     const int* __restrict__ ccs, const int* __restrict__ chunk_cell, int total_cells,
     const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base, int n_vol,
     float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
-    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi) {
+    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, const unsigned char* __restrict__ active) {
     constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
     const int n_chunks = ccs[total_cells];
@@ -230,6 +233,9 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
                 }
             }
         }
+        int nact = 0;
+#pragma unroll
+        for (int s = 0; s < K; ++s) nact += __popc(__ballot_sync(kFull, valid[s] && (!active || active[orig[s]])));
         int qa[3];
         float bl[3], bh[3];
 #pragma unroll
@@ -252,7 +258,8 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
                 }
             }
             const long long slot = (long long)k * C + lane + 32 * s;
-            slot_pos[slot] = make_float4(off[0], off[1], off[2], valid[s] ? 1.0f : 0.0f);
+            const float w = !valid[s] ? 0.0f : (!active || active[orig[s]]) ? 1.0f : -1.0f;
+            slot_pos[slot] = make_float4(off[0], off[1], off[2], w);
             slot_idx[slot] = orig[s];
         }
 #pragma unroll
@@ -267,14 +274,14 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
             const int cnt = min(C, n_cell - r0);
             chunk_meta[k] = make_int4(qa[0], qa[1], qa[2], v);
             chunk_lo[k] = make_float4(bl[0], bl[1], bl[2], __int_as_float(cnt));
-            chunk_hi[k] = make_float4(bh[0], bh[1], bh[2], 0.0f);
+            chunk_hi[k] = make_float4(bh[0], bh[1], bh[2], __int_as_float(nact));
         }
     }
 }
 
 }  // namespace
 
-int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st) {
+int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, const unsigned char* active) {
     const int b = p->sub_bits;
     const int ni = (int)n;
     if (ni > 0) {
@@ -301,11 +308,11 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st) {
     if (p->chunk_k == 2)
         k_chunk_fill<2><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
                                                 p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
-                                                p->chunk_meta, p->chunk_lo, p->chunk_hi);
+                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active);
     else
         k_chunk_fill<1><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
                                                 p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
-                                                p->chunk_meta, p->chunk_lo, p->chunk_hi);
+                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active);
     SR_LAUNCH_CHECK("k_chunk_fill");
     return launch_cost_and_order(p, st);
 }

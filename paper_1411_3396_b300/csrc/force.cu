@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
     const unsigned lt = lanemask_lt();
     float4* rp = ring_p[warp];
     float4* rg = ring_g[MODE == kVjp ? warp : 0];
-    const int n_items = a.ccs[a.total_cells];
+    const int n_items = (int)a.ctr->n_items;       // chunks holding an active particle, in a.order
     while (true) {
         int it_idx = 0;
         if (lane == 0) it_idx = (int)atomicAdd((unsigned long long*)&a.ctr->queue, 1ull);
@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int l = lane + 32 * k;
-            if (l < it.cnt) {
+            // active particles only (slot w = 1; a passive neighbour's row is left untouched)
+            if (l < it.cnt && a.slot_pos[(long long)I * C + l].w > 0.f) {
                 const int orig = a.slot_idx[(long long)I * C + l];
                 const float ox = (w.sx[k] - w.cx[k]) * KC.scale;
                 const float oy = (w.sy[k] - w.cy[k]) * KC.scale;
@@ -380,16 +381,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
 // Cost estimate of each work item, for the longest-first order: the
 // chunk's particle count times the population of the neighbour cells its
 // box reaches (the same cell culling as the pair kernel).  One thread per
-// chunk; chunks beyond the current count get the lowest priority key.
+// chunk; chunks beyond the current count, and chunks without an active
+// particle, get the key after every other (they are never work items);
+// the work items are counted into ctr->n_items.
 __global__ void __launch_bounds__(256) k_cost(const Args a, int max_chunks, unsigned* __restrict__ cost,
                                               unsigned long long* __restrict__ keys, int* __restrict__ vals) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_chunks = a.ccs[a.total_cells];
     unsigned long long cst = 0;
-    if (I < max_chunks && I >= n_chunks) {
+    const bool item = I < n_chunks && __float_as_int(a.chi[I].w) > 0;
+    if (I < max_chunks && !item) {
         keys[I] = 255ull;
         vals[I] = I;
-    } else if (I < n_chunks) {
+        if (I < n_chunks) cost[I] = 0u;
+    } else if (item) {
         const Item it = load_item(a, I);
         const VolDev& V = a.vols[it.vol];
         int c[3], olo[3], ohi[3];
@@ -425,7 +430,11 @@ __global__ void __launch_bounds__(256) k_cost(const Args a, int max_chunks, unsi
     // launch is alive here; lanes past the chunks add 0)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cst += __shfl_xor_sync(kFull, cst, o);
-    if ((threadIdx.x & 31) == 0 && cst) atomicAdd(&a.ctr->cost_total, cst);
+    const int items = __popc(__ballot_sync(kFull, item));
+    if ((threadIdx.x & 31) == 0) {
+        if (cst) atomicAdd(&a.ctr->cost_total, cst);
+        if (items) atomicAdd((unsigned long long*)&a.ctr->n_items, (unsigned long long)items);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_gather_g(const float* __restrict__ g, const int* __restrict__ slot_idx,
@@ -534,6 +543,7 @@ int force_occupancy(sr_plan* p) {
 int launch_cost_and_order(sr_plan* p, cudaStream_t st) {
     Args a = make_args(p);
     SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->cost_total, 0, sizeof(unsigned long long), st));
+    SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->n_items, 0, sizeof(long long), st));
     const long long mc = p->max_chunks;
     k_cost<<<(int)((mc + 255) / 256), 256, 0, st>>>(a, (int)mc, p->cost, p->lpt_keys[0], p->lpt_vals[0]);
     SR_LAUNCH_CHECK("k_cost");

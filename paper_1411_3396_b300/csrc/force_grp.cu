@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
     const int il = lane & (G - 1);
     const int jp = lane / G;
     const int mygrp = lane / G;          // the group that slot `lane` belongs to
-    const int n_items = a.ccs[a.total_cells];
+    const int n_items = (int)a.ctr->n_items;       // chunks holding an active particle, in a.order
     while (true) {
         int it_idx = 0;
         if (lane == 0) it_idx = (int)atomicAdd((unsigned long long*)&a.ctr->queue, 1ull);
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
         }
 
         int cpairs = 0;
-        if (valid) {
+        if (valid && pi.w > 0.f) {                                  // active particles only
             const int orig = a.slot_idx[(long long)I * 32 + lane];
             const float ox = (sx - cx) * KC.scale;
             const float oy = (sy - cy) * KC.scale;

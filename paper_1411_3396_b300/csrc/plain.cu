@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(128) k_plain(const int* __restrict__ ccs, cons
     if (lane >= cnt) return;
     const VolDev& V = vols[mi.w];
     const float4 pi = slot_pos[s];
+    if (pi.w <= 0.f) return;                           // a passive neighbour: its row is not written
     const int b = V.sub_bits;
     const int cx = mi.x >> b, cy = mi.y >> b, cz = mi.z >> b;
     const float eps2 = V.eps2u, rc2 = V.rc2u;

@@ -136,7 +136,8 @@ struct Counters {
     unsigned long long cost_total;
     unsigned long long evals;         // counting variant: candidate (i, j) evaluations, valid i only
     unsigned long long lane_evals;    // counting variant: candidate evaluations x 32 lanes
-    long long reserved[3];
+    long long n_items;                // work items of the pair kernels: chunks holding an active particle
+    long long reserved[2];
 };
 
 struct ScanScratch {
@@ -250,7 +251,8 @@ int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_b
                      RadixScratch& r, cudaStream_t st, int* which);
 
 // binning (bin.cu)
-int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st);
+int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st,
+               const unsigned char* active = nullptr);
 
 // force, cost, order, vjp (force.cu)
 int launch_cost_and_order(sr_plan* p, cudaStream_t st);

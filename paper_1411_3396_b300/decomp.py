@@ -11,11 +11,13 @@ Cells are at least r_c wide and the pair kernel reads only the 27 cells
 around a particle's own, so one ghost cell on each side of the slab holds
 every neighbour within r_c.  Cell membership here follows the binning
 kernel's definition exactly (fold into [0, L), t = x / h in binary64,
-q = min(floor(t), M - 1), cell = q >> b), and the local particles are kept
-in increasing global-id order; the binning sort is stable, so every cell an
-owned particle reads holds the same particles in the same order as in the
-undivided volume, and the owned particles' forces are bit-identical to the
-single-volume result.
+q = min(floor(t), M - 1), cell = q >> b), and every cell's particles are
+kept in increasing global-id order; the binning sort is stable, so every
+cell an owned particle reads holds the same particles in the same order as
+in the undivided volume, and the owned particles' forces are bit-identical
+to the single-volume result.  The ghosts are binned with an active mask
+(Plan.bin(pos, active=owned)): only chunks holding owned particles are work
+items of the pair kernels, and only owned rows are written.
 
 Index bookkeeping (cells, masks, selection, ordering) runs in PyTorch on the
 tensors' device, and the exchange in torch.distributed (gloo or NCCL); this
@@ -99,28 +101,40 @@ class Slabs:
 
     def exchange(self, pos: torch.Tensor, ids: torch.Tensor, group=None):
         """Overload exchange between ranks that each hold exactly their owned
-        particles (pos, ids): returns this rank's owned + ghost particles
-        (positions, global ids, owned flags) in increasing global-id order.
-        One all-gather of the send counts, then point-to-point sends to
-        every rank of the particles in the cells next to its slab."""
+        particles (pos, ids), in increasing global-id order (as migrate
+        returns them): returns this rank's owned + ghost particles
+        (positions, global ids, owned flags): its own particles first, as
+        given, then the ghosts of each other rank in rank order, each in that
+        rank's order.  A cell belongs wholly to one slab, so every cell's
+        particles arrive from one rank in increasing id order, which is all
+        the stable binning needs for the owned forces to equal the undivided
+        volume's bit for bit; no sort.  One all-gather of the send counts
+        (read on the host once), then point-to-point sends to every rank of
+        the particles in the cells next to its slab."""
         import torch.distributed as dist
         world = dist.get_world_size(group)
         rank = dist.get_rank(group)
         if world != self.world:
             raise ValueError("slab count differs from the process group size")
         dev = pos.device
-        sends = [None if q == rank else torch.nonzero(self.ghost(pos, q)).squeeze(1)
-                 for q in range(world)]
-        counts = torch.tensor([0 if s is None else len(s) for s in sends], dtype=torch.int64, device=dev)
+        # every peer's ghost rows in one selection (rows grouped by peer, in
+        # increasing row order within each)
+        none = torch.zeros(len(pos), dtype=torch.bool, device=dev)
+        masks = torch.stack([none if q == rank else self.ghost(pos, q) for q in range(world)])
+        peer, rows = masks.nonzero(as_tuple=True)
+        counts = torch.bincount(peer, minlength=world)
         table = [torch.zeros_like(counts) for _ in range(world)]
         dist.all_gather(table, counts, group=group)
+        table = torch.stack(table).tolist()                   # one device-to-host read: all counts
+        sends = list(torch.split(rows, table[rank]))
+        incoming = [table[q][rank] for q in range(world)]
         # one batch of point-to-point operations (grouped, so that NCCL does
         # not block on the first receive while its peer waits on its own)
         recv_pos, recv_ids, ops = [], [], []
         for q in range(world):
             if q == rank:
                 continue
-            nq = int(table[q][rank].item())
+            nq = int(incoming[q])
             rp = torch.empty((nq, 3), dtype=pos.dtype, device=dev)
             ri = torch.empty(nq, dtype=ids.dtype, device=dev)
             recv_pos.append(rp)
@@ -134,12 +148,9 @@ class Slabs:
         if ops:
             for r in dist.batch_isend_irecv(ops):
                 r.wait()
-        all_pos = torch.cat([pos] + recv_pos)
-        all_ids = torch.cat([ids] + recv_ids)
-        own = torch.cat([torch.ones(len(pos), dtype=torch.bool, device=dev)] +
-                        [torch.zeros(len(r), dtype=torch.bool, device=dev) for r in recv_ids])
-        order = torch.argsort(all_ids)
-        return all_pos[order].contiguous(), all_ids[order].contiguous(), own[order].contiguous()
+        own = torch.zeros(len(pos) + sum(len(r) for r in recv_ids), dtype=torch.bool, device=dev)
+        own[:len(pos)] = True
+        return torch.cat([pos] + recv_pos).contiguous(), torch.cat([ids] + recv_ids).contiguous(), own
 
     def migrate(self, pos: torch.Tensor, ids: torch.Tensor, *fields: torch.Tensor, group=None):
         """Hand every particle to the rank whose slab holds it, after a drift
@@ -147,8 +158,12 @@ class Slabs:
         within one period of [0, box)).  `fields` are per-particle arrays
         (velocities, accelerations, ...) that travel with the positions.
         Returns (pos, ids, *fields) of the particles this rank owns, in
-        increasing global-id order.  One all-gather of the send counts, then
-        one batch of point-to-point sends to the ranks that gain particles."""
+        increasing global-id order: after a drift a cell can hold kept and
+        received particles together, and the stable binning needs each
+        cell's particles in id order, so the merged set is sorted by id here
+        (once per migration; the exchange then needs no sort).  One
+        all-gather of the send counts (read on the host once), then one batch
+        of point-to-point sends to the ranks that gain particles."""
         import torch.distributed as dist
         world = dist.get_world_size(group)
         rank = dist.get_rank(group)
@@ -159,17 +174,19 @@ class Slabs:
         dev = pos.device
         dest = self.owner(pos)
         arrays = (pos, ids) + fields
-        sends = [torch.nonzero(dest == q).squeeze(1) for q in range(world)]
-        counts = torch.tensor([0 if q == rank else len(sends[q]) for q in range(world)],
-                              dtype=torch.int64, device=dev)
+        rows = torch.argsort(dest, stable=True)                # rows grouped by new owner
+        counts = torch.bincount(dest, minlength=world)
         table = [torch.zeros_like(counts) for _ in range(world)]
         dist.all_gather(table, counts, group=group)
+        table = torch.stack(table).tolist()                   # one device-to-host read: all counts
+        sends = list(torch.split(rows, table[rank]))
+        incoming = [0 if q == rank else table[q][rank] for q in range(world)]
         kept = [a[sends[rank]] for a in arrays]
         recv, ops = [], []
         for q in range(world):
             if q == rank:
                 continue
-            nq = int(table[q][rank].item())
+            nq = int(incoming[q])
             bufs = [torch.empty((nq,) + tuple(a.shape[1:]), dtype=a.dtype, device=dev) for a in arrays]
             recv.append(bufs)
             if nq:

@@ -87,6 +87,25 @@ def test_owner_matches_owned_masks():
             assert torch.equal(own == r, s.owned(x, r))
 
 
+def _matches_local_set(got, want, s, box, own_in):
+    """The exchange's result holds the selection's particles (the same rows
+    once sorted by id), its own particles first as given, and every cell's
+    particles in increasing id order (what the stable binning needs)."""
+    pos, ids, own = got
+    order = torch.argsort(ids)
+    ok = all(torch.equal(a[order], b) for a, b in zip(got, want))
+    ok &= torch.equal(pos[:len(own_in[0])], own_in[0]) and torch.equal(ids[:len(own_in[1])], own_in[1])
+    ok &= bool(own[:len(own_in[1])].all()) and not bool(own[len(own_in[1]):].any())
+    _, q = obin.fine_coords(pos.numpy(), box, s.n_cells, s.sub_bits)
+    c = q >> s.sub_bits
+    cell = (c[:, 2] * s.n_cells + c[:, 1]) * s.n_cells + c[:, 0]
+    key = np.lexsort((np.arange(len(cell)), cell))         # rows of each cell, in the returned order
+    same = cell[key][1:] == cell[key][:-1]
+    idn = ids.numpy()[key]
+    ok &= bool(np.all(idn[1:][same] > idn[:-1][same]))
+    return bool(ok)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -106,12 +125,11 @@ def _worker(rank, world, port, q):
         ids = torch.arange(len(pos), dtype=torch.int64)
         s = Slabs(box, 6, 0, world)
         mine = s.owned(pos, rank)
-        # every rank starts with its owned particles only, in a scrambled order
-        perm = torch.randperm(int(mine.sum()), generator=torch.Generator().manual_seed(rank))
-        p0, i0 = pos[mine][perm], ids[mine][perm]
+        # every rank starts with its owned particles only, in id order
+        p0, i0 = pos[mine], ids[mine]
         got = s.exchange(p0, i0)
         want = s.local_set(pos, ids, rank)
-        ok = all(torch.equal(a, b) for a, b in zip(got, want))
+        ok = _matches_local_set(got, want, s, box, (p0, i0))
         q.put((rank, ok, int(got[2].sum()), len(got[1])))
     finally:
         dist.destroy_process_group()
@@ -165,7 +183,7 @@ def _migrate_worker(rank, world, port, q):
             ok &= torch.equal(i, ids[want]) and torch.equal(p, pos[want]) and torch.equal(v, vel[want])
             ok &= lb.dtype == torch.int32 and torch.equal(lb, lab[want])
             got = s.exchange(p, i)
-            ok &= all(torch.equal(a, b) for a, b in zip(got, s.local_set(pos, ids, rank)))
+            ok &= _matches_local_set(got, s.local_set(pos, ids, rank), s, box, (p, i))
         q.put((rank, bool(ok), len(i), moved))
     finally:
         dist.destroy_process_group()
@@ -186,3 +204,77 @@ def test_migrate_gloo(world):
     assert all(ok for _, ok, _, _ in res), res
     assert sum(n for _, _, n, _ in res) == 6000
     assert all(m > 0 for _, _, _, m in res)
+
+
+def _slab_step_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import torch.distributed as dist
+
+    import bench
+    from oracle import fit as ofit
+    from oracle import force as oforce
+    from paper_1411_3396_b300.decomp import Slabs
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        box, rc, eps, dt = 24.0, 3.0, 0.1, 0.01
+        pos = torch.from_numpy(_clustered(box=box))
+        n = len(pos)
+        s = Slabs(box, 6, 0, world)
+        mine = s.owned(pos, rank)
+        x_own, ids_own = pos[mine], torch.arange(n)[mine]
+        n_own = len(x_own)
+        vel = torch.zeros((n, 4), dtype=torch.float32)
+        vel[:n_own, :3] = torch.from_numpy(np.random.default_rng(3).normal(size=(n, 3))[mine.numpy()]).float()
+        v0 = vel[:n_own].clone()
+        acc = torch.full((n, 4), float("nan"), dtype=torch.float32)
+        c = ofit.fit_poly(rc, 0.8, eps)
+        got = {}
+
+        def force_kick(xl, own, a, v):
+            # the FP64 oracle stands in for the kernels: each owned row gets
+            # the force from every local particle (its slab and the ghosts)
+            ref, _ = oforce.accel_kdtree(xl.numpy(), box, rc, eps, c)
+            o = own.numpy()
+            got["own"] = ref[o]
+            a[own, :3] = torch.from_numpy(ref[o]).float()
+            a[own, 3] = 0.0
+            v[own, :3] += a[own, :3] * dt
+            got["m"], got["n_own_flags"] = len(xl), int(o.sum())
+
+        m = bench.slab_step(s, x_own, ids_own, acc, vel, force_kick)
+        untouched = bool(torch.isnan(acc[n_own:]).all())
+        kicked = bool(torch.equal(vel[:n_own, :3], v0[:, :3] + acc[:n_own, :3] * dt))
+        q.put((rank, ids_own.numpy(), got["own"], m, got["m"], got["n_own_flags"] == n_own, untouched, kicked))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_bench_slab_step_gloo(world):
+    # the bench's multi-GPU step (exchange, passive ghosts, owned rows
+    # written and kicked), driven with gloo ranks on the CPU and the oracle
+    # in place of the kernels: the ranks' owned forces assemble the
+    # undivided volume's forces
+    from oracle import fit as ofit
+    from oracle import force as oforce
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_step_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=180) for _ in range(world)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    pos = _clustered(box=24.0)
+    ref, _ = oforce.accel_kdtree(pos, 24.0, 3.0, 0.1, ofit.fit_poly(3.0, 0.8, 0.1))
+    full = np.full_like(ref, np.nan)
+    for rank, ids, own_acc, m, m_seen, flags_ok, untouched, kicked in res:
+        assert m == m_seen and flags_ok and untouched and kicked
+        assert m > len(ids)                                  # ghosts arrived
+        full[ids] = own_acc
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(full, ref, rtol=0, atol=1e-12 * scale)

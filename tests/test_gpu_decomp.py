@@ -21,38 +21,73 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _force(pos, box, prm, n_cells, chunk):
+def _force(pos, box, prm, n_cells, chunk, active=None, variant=None):
     from paper_1411_3396_b300 import Plan
     plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], len(pos), n_cells=n_cells, chunk_size=chunk)
-    plan.bin(pos)
-    acc, pairs, pp = plan.force(count=True, per_particle=True)
+    plan.bin(pos, active=active)
+    if variant is not None:
+        plan.set_variant(variant)
+    # sentinels: rows the kernels must not write (passive particles) keep them
+    acc = torch.full((len(pos), 4), float("nan"), dtype=torch.float32, device="cuda")
+    pp = torch.full((len(pos),), -7, dtype=torch.int32, device="cuda")
+    acc, pairs, pp = plan.force(acc, count=True, per_particle=pp)
     torch.cuda.synchronize()
     return plan, acc, int(pairs.item()), pp
 
 
-def _check_ranks(pos_np, box, prm, world, chunk):
+def _check_ranks(pos_np, box, prm, world, chunk, active=False, variant=None):
+    """Every rank's owned + ghost set forced in a plan of the whole box; with
+    active, the ghosts are binned as passive (sr_bin_active): then only the
+    chunks holding owned particles are work items, so the ranks' candidate
+    evaluations add up to the whole volume's, and ghost rows stay unwritten."""
     from paper_1411_3396_b300.decomp import Slabs
     pos = torch.from_numpy(pos_np).cuda()
-    plan, acc_full, pairs_full, pp_full = _force(pos, box, prm, 0, chunk)
+    plan, acc_full, pairs_full, pp_full = _force(pos, box, prm, 0, chunk, variant=variant)
+    ctr_full = plan.export("counters").cpu().numpy()
     slabs = Slabs.of_plan(plan, world)
     n_c = plan.volume(0)["n_cells"]
+    n_chunks = plan.info()["n_chunks"]
     assert slabs.h == plan.volume(0)["h"]
     plan.close()
     ids_all = torch.arange(len(pos), device="cuda")
     seen = torch.zeros(len(pos), dtype=torch.int32, device="cuda")
-    pairs_owned = 0
+    pairs_owned = pairs_sum = evals = items = 0
     for r in range(world):
         p, ids, own = slabs.local_set(pos, ids_all, r)
-        pl, acc, _, pp = _force(p, box, prm, n_c, chunk)
+        pl, acc, pairs, pp = _force(p, box, prm, n_c, chunk, active=own if active else None, variant=variant)
+        ctr = pl.export("counters").cpu().numpy()
         pl.close()
         mine = ids[own]
         assert torch.equal(acc[own], acc_full[mine]), f"rank {r}: forces differ from the whole volume"
         assert torch.equal(pp[own], pp_full[mine])
         seen[mine] += 1
         pairs_owned += int(pp[own].sum().item())
+        pairs_sum += pairs
+        evals += int(ctr[3])
+        items += int(ctr[5])
+        if active:
+            assert torch.all(torch.isnan(acc[~own])), f"rank {r}: a passive row was written"
+            assert torch.all(pp[~own] == -7)
     assert torch.all(seen == 1)
     assert pairs_owned == pairs_full
+    if active:
+        assert pairs_sum == pairs_full                 # the pair total counts owned rows only
+        assert evals == int(ctr_full[3])               # no evaluation spent on passive chunks
+        assert items == n_chunks == int(ctr_full[5])
+    else:
+        assert evals > int(ctr_full[3])                # ghost chunks forced and thrown away
     return to_np(acc_full)
+
+
+@pytest.mark.parametrize("variant", [None, 14, 15])
+@pytest.mark.parametrize("world", [2, 3])
+def test_slabs_with_passive_ghosts(world, variant):
+    w = wc.make_workload(wc.small_variant("clustered256"))
+    (pos, box), = w["volumes"]
+    _check_ranks(pos, box, w["params"], world, 32, active=True, variant=variant)
+    w = wc.make_workload(wc.small_variant("zeldovich128"))
+    (pos, box), = w["volumes"]
+    _check_ranks(pos, box, w["params"], world, 32, active=True, variant=variant)
 
 
 @pytest.mark.parametrize("world", [2, 3, 4])

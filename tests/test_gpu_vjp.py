@@ -159,12 +159,28 @@ def test_trajectory_full_size_64cubed():
             (np.median(rel), norm, rel.max())
 
 
+def _rows_straddling_the_cutoff(x, box, rc, rel=1e-6):
+    """Rows with a neighbour at a distance within rel of r_c.  The force is
+    continuous at r_c but its derivative is not (f(r_c^2) = 0, f'(r_c^2) !=
+    0), so the VJP of such a pair jumps by a term of its own size where the
+    binary32 predicate of the kernel and the FP64 one of the oracle decide
+    on different sides (the offsets' binary32 representation moves s by
+    about 2e-7 relative)."""
+    from scipy.spatial import cKDTree
+    t = cKDTree(np.mod(x, box), boxsize=box)
+    hi = t.query_ball_point(np.mod(x, box), rc * (1 + rel), return_length=True)
+    lo = t.query_ball_point(np.mod(x, box), rc * (1 - rel), return_length=True)
+    return hi > lo
+
+
 def test_vjp_per_substep_on_gpu_states_64cubed():
     # separates the VJP kernel's own error from trajectory divergence at full
     # size: each substep's GPU VJP is compared, at the force bar, with the
     # oracle's VJP at the GPU's own state x_k and the GPU's own cotangent
     # (the binary32 dt * vbar the kernel applies); the end-to-end bar of
-    # test_trajectory_full_size_64cubed covers the whole trajectory
+    # test_trajectory_full_size_64cubed covers the whole trajectory.  Rows
+    # with a pair straddling r_c (a few hundred of 262,144) are left out of
+    # the comparison: there the VJP has a jump of the size of one pair term
     from paper_1411_3396_b300 import Plan, kick
     cfg = wc.CONFIGS["diff64"]
     box, n_side, steps, dt = cfg["box"], cfg["n_side"], cfg["steps"], cfg["dt"]
@@ -194,8 +210,11 @@ def test_vjp_per_substep_on_gpu_states_64cubed():
         plan.bin(states[k])
         out = plan.vjp(vbar, g_scale=dt)
         g = (to_np(vbar)[:, :3] * np.float32(dt)).astype(np.float64)
-        ref = oint.force_vjp(to_np(states[k]), box, rc, eps, c, g)
-        assert_force_close(to_np(out), ref, f"vjp of substep {k}")
+        xk = to_np(states[k])
+        ref = oint.force_vjp(xk, box, rc, eps, c, g)
+        edge = _rows_straddling_the_cutoff(xk, box, rc)
+        assert edge.sum() <= 2e-3 * n, edge.sum()
+        assert_force_close(to_np(out)[~edge], ref[~edge], f"vjp of substep {k}")
         xbar += out
 
 
