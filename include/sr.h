@@ -48,6 +48,7 @@ extern "C" {
 #define SR_ERR_STATE     4   /* call order violated (e.g. sr_force before sr_bin) */
 #define SR_ERR_RANGE     5   /* a position was non-finite or outside [-L, 2L) */
 #define SR_ERR_TIMEOUT   6   /* a bounded device-side loop ran out of iterations (see the call) */
+#define SR_ERR_CHECK     7   /* bounds-checked build: an index check failed (the access was skipped) */
 
 /* Polynomial fit modes. */
 #define SR_FIT_CONSTRAINED    0  /* least squares with p(r_c^2) = (r_c^2+eps^2)^(-3/2): f_SR(r_c^2) = 0 */
@@ -312,10 +313,29 @@ int sr_invariants_noalloc(int64_t n, const float* vel, const float* acc, double*
 
 /*
  * sr_plan_status -- synchronise the stream and report device-side flags of
- * the last calls: SR_ERR_RANGE if sr_bin saw a non-finite or out-of-range
- * position (the flag is then cleared), else SR_OK.
+ * the last calls: SR_ERR_CHECK if a bounds check of the checked build failed,
+ * else SR_ERR_RANGE if sr_bin saw a non-finite or out-of-range position (the
+ * reported flag is then cleared), else SR_OK.
  */
 int sr_plan_status(sr_plan* plan, void* stream);
+
+/*
+ * The bounds-checked build (libsr_b300_check.so, compiled with -DSR_CHECK;
+ * same entry points, slower).  Its pair kernels, binning kernels, radix
+ * scatter and center finder check every work-item, cell, chunk, ring, list,
+ * caller-row and slot index before the access; a failed check records its
+ * code in the plan's error word (the first one is kept), skips the access
+ * and never traps, and sr_plan_status then returns SR_ERR_CHECK with the
+ * code in sr_last_error (sr_centers_info.check_code for the center
+ * finder).  The release build compiles none of the checks.
+ * sr_build_checked -- 1 in the bounds-checked build, 0 in the release build.
+ * sr_check_selftest -- records check code 99 without any memory access (a
+ * check whose condition is false), so that the next sr_plan_status returns
+ * SR_ERR_CHECK in the bounds-checked build; in the release build it does
+ * nothing.  Enqueued on stream.  Errors: SR_ERR_ARG (null plan).
+ */
+int sr_build_checked(void);
+int sr_check_selftest(sr_plan* plan, void* stream);
 
 /*
  * sr_plan_copy -- copy one internal array of the last sr_bin (selector

@@ -54,6 +54,8 @@ typedef struct sr_centers_info {
     int32_t variant;          /* SR_CENTERS_*                                         */
     int64_t bad_labels;       /* labels < -1 or >= n_halos (treated as -1)            */
     int64_t wide_members;     /* members farther than L/4 from their halo's first one */
+    int64_t check_code;       /* bounds-checked build (sr_build_checked): code of the
+                                 first failed bounds check of the last run, 0 = none */
 } sr_centers_info;
 
 /*

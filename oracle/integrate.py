@@ -33,8 +33,11 @@ def drift(x, v, dt, box):
     return _wrap_for_tree(np.asarray(x, np.float64) + np.asarray(v, np.float64) * dt, box)
 
 
-def force_vjp(pos, box, rc, eps, c, gbar):
-    """xbar = (da/dx)^T gbar for the short-range accelerations."""
+def force_vjp(pos, box, rc, eps, c, gbar, absolute=False):
+    """xbar = (da/dx)^T gbar for the short-range accelerations.  With
+    absolute, also the per-row sums of the terms' magnitudes, sum_j |w_ij|
+    per axis (the scale of the rounding error of any evaluation of the sum
+    in finite precision)."""
     pos = _wrap_for_tree(pos, box)
     gbar = np.asarray(gbar, np.float64)
     n = len(pos)
@@ -52,7 +55,13 @@ def force_vjp(pos, box, rc, eps, c, gbar):
     for ax in range(3):
         out[:, ax] = np.bincount(i, weights=w[:, ax], minlength=n) - \
             np.bincount(j, weights=w[:, ax], minlength=n)
-    return out
+    if not absolute:
+        return out
+    mag = np.zeros((n, 3))
+    for ax in range(3):
+        aw = np.abs(w[:, ax])
+        mag[:, ax] = np.bincount(i, weights=aw, minlength=n) + np.bincount(j, weights=aw, minlength=n)
+    return out, mag
 
 
 def trajectory(x0, v0, box, rc, eps, c, dt, steps, accel=None):

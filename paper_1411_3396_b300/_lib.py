@@ -5,9 +5,11 @@ from __future__ import annotations
 import ctypes
 from ctypes import POINTER, c_double, c_float, c_int, c_int64, c_uint64, c_void_p, c_char_p
 
-from .build import LIB
+import os
 
-SR_OK, SR_ERR_ARG, SR_ERR_CUDA, SR_ERR_CAPACITY, SR_ERR_STATE, SR_ERR_RANGE, SR_ERR_TIMEOUT = range(7)
+from .build import LIB, LIB_CHECKED
+
+SR_OK, SR_ERR_ARG, SR_ERR_CUDA, SR_ERR_CAPACITY, SR_ERR_STATE, SR_ERR_RANGE, SR_ERR_TIMEOUT, SR_ERR_CHECK = range(8)
 FIT_MODES = {"constrained": 0, "unconstrained": 1}
 EXPORTS = {
     "perm": 0, "cell_start": 1, "cell_chunk_start": 2, "slot_pos": 3, "slot_idx": 4,
@@ -33,7 +35,7 @@ class SrCentersInfo(ctypes.Structure):
     _fields_ = [("n_particles", c_int64), ("n_members", c_int64), ("n_halos", c_int64),
                 ("max_members", c_int64), ("pairs", c_int64), ("items", c_int64),
                 ("evaluated", c_int64), ("fixed_shift", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("bad_labels", c_int64), ("wide_members", c_int64)]
+                ("bad_labels", c_int64), ("wide_members", c_int64), ("check_code", c_int64)]
 
 
 class SrFofInfo(ctypes.Structure):
@@ -73,6 +75,8 @@ SIGNATURES = {
     "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
     "sr_bin_active": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "sr_variant_count": (c_int, []),
+    "sr_build_checked": (c_int, []),
+    "sr_check_selftest": (c_int, [c_void_p, c_void_p]),
     "sr_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
     "sr_graph_launch": (c_int, [c_void_p, c_void_p]),
     "sr_centers_create": (c_int, [c_int64, ctypes.c_int32, POINTER(c_void_p)]),
@@ -106,12 +110,15 @@ _lib = None
 
 
 def load():
-    """Load libsr_b300.so (built in-tree by __graft_entry__.build())."""
+    """Load libsr_b300.so (built in-tree by __graft_entry__.build()), or the
+    bounds-checked libsr_b300_check.so when SR_B300_CHECKED=1 is set in the
+    environment of the process before the first call."""
     global _lib
     if _lib is None:
-        if not LIB.exists():
-            raise RuntimeError(f"{LIB.name} is not built; run __graft_entry__.build() first")
-        lib = ctypes.CDLL(str(LIB))
+        path = LIB_CHECKED if os.environ.get("SR_B300_CHECKED") == "1" else LIB
+        if not path.exists():
+            raise RuntimeError(f"{path.name} is not built; run __graft_entry__.build() first")
+        lib = ctypes.CDLL(str(path))
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)
             fn.restype = res

@@ -18,6 +18,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 LIB = PKG / "libsr_b300.so"
+LIB_CHECKED = PKG / "libsr_b300_check.so"     # bounds-checked build (-DSR_CHECK)
 SOURCES = ["abi.cu", "fit.cpp", "radix.cu", "bin.cu", "force.cu", "force_grp.cu", "plain.cu", "kick.cu", "noalloc.cu",
            "centers.cu", "pm.cu", "fof.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,34 +36,54 @@ def _inputs():
     return files
 
 
-def needs_build() -> bool:
-    if not LIB.exists():
+def needs_build(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return True
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     return any(f.stat().st_mtime > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> Path:
-    """Compile every source to an object (in parallel), then link."""
-    if not force and not needs_build():
-        return LIB
-    tmp = LIB.with_suffix(".so.tmp")
-    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE), *(extra or [])]
+def _compile(targets, verbose, extra):
+    """Compile every source of each (library, extra flags) target to objects
+    (all in parallel), then link each library."""
     with tempfile.TemporaryDirectory(prefix="sr_build_") as d:
-        objs = [os.path.join(d, s + ".o") for s in SOURCES]
-        cmds = [[_nvcc(), *flags, "-c", str(CSRC / s), "-o", o] for s, o in zip(SOURCES, objs)]
-        with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
-            results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), cmds))
-        link = [_nvcc(), *ARCH, "-shared", "-o", str(tmp), *objs]
-        results.append(subprocess.run(link, capture_output=True, text=True))
-        for cmd, res in zip(cmds + [link], results):
+        jobs, links = [], []
+        for k, (lib, flags_extra) in enumerate(targets):
+            flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE),
+                     *flags_extra, *(extra or [])]
+            objs = [os.path.join(d, f"{k}_{s}.o") for s in SOURCES]
+            jobs += [[_nvcc(), *flags, "-c", str(CSRC / s), "-o", o] for s, o in zip(SOURCES, objs)]
+            links.append((lib, [_nvcc(), *ARCH, "-shared", "-o", str(lib.with_suffix(".so.tmp")), *objs]))
+        with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+            results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
+        for cmd, res in zip(jobs, results):
             if verbose or res.returncode != 0:
                 print(" ".join(cmd))
                 print(res.stdout)
                 print(res.stderr)
             if res.returncode != 0:
-                raise RuntimeError("nvcc failed building libsr_b300.so:\n" + res.stderr[-4000:])
-    os.replace(tmp, LIB)
+                raise RuntimeError("nvcc failed building the library:\n" + res.stderr[-4000:])
+        for lib, cmd in links:
+            res = subprocess.run(cmd, capture_output=True, text=True)
+            if verbose or res.returncode != 0:
+                print(" ".join(cmd))
+                print(res.stdout)
+                print(res.stderr)
+            if res.returncode != 0:
+                raise RuntimeError("nvcc failed linking " + lib.name + ":\n" + res.stderr[-4000:])
+            os.replace(lib.with_suffix(".so.tmp"), lib)
+
+
+def build(force: bool = False, verbose: bool = False, extra=None, checked: bool = True) -> Path:
+    """Build libsr_b300.so and (checked=True) the bounds-checked
+    libsr_b300_check.so where a source is newer than the library."""
+    targets = []
+    if force or needs_build(LIB):
+        targets.append((LIB, []))
+    if checked and (force or needs_build(LIB_CHECKED)):
+        targets.append((LIB_CHECKED, ["-DSR_CHECK"]))
+    if targets:
+        _compile(targets, verbose, extra)
     return LIB
 
 

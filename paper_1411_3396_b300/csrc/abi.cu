@@ -428,12 +428,34 @@ int sr_plan_status(sr_plan* p, void* stream) {
     cudaStream_t st = as_stream(stream);
     SR_CUDA_CHECK(cudaMemcpyAsync(&err, &p->ctr->err, sizeof(long long), cudaMemcpyDeviceToHost, st));
     SR_CUDA_CHECK(cudaStreamSynchronize(st));
+    unsigned long long chk = 0;
+    SR_CUDA_CHECK(cudaMemcpyAsync(&chk, &p->ctr->check, sizeof(chk), cudaMemcpyDeviceToHost, st));
+    SR_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (chk) {
+        SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->check, 0, sizeof(chk), st));
+        SR_CUDA_CHECK(cudaStreamSynchronize(st));
+        return set_error(SR_ERR_CHECK, "bounds check " + std::to_string(chk) +
+                                           " failed (bounds-checked build); the access was skipped");
+    }
     if (err & 1) {
         SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->err, 0, sizeof(long long), st));
         SR_CUDA_CHECK(cudaStreamSynchronize(st));
         return set_error(SR_ERR_RANGE, "sr_bin saw a non-finite position or one outside [-L, 2L)");
     }
     return SR_OK;
+}
+
+int sr_build_checked(void) {
+#ifdef SR_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int sr_check_selftest(sr_plan* p, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    return launch_check_selftest(p, as_stream(stream));
 }
 
 int sr_plan_copy(sr_plan* p, int which, void* dst, int64_t bytes, void* stream) {

@@ -149,17 +149,21 @@ __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, in
     const int cell = V.cell_base + ((q[2] >> b) * V.n_c + (q[1] >> b)) * V.n_c + (q[0] >> b);
     const unsigned long long m = spread3(q[0] & mask) | (spread3(q[1] & mask) << 1) |
                                  (spread3(q[2] & mask) << 2);
+    if (!SR_BOUND(cell >= V.cell_base && cell < V.cell_base + V.n_c * V.n_c * V.n_c, &ctr->check, kChkKeyCell))
+        return;
     keys[i] = ((unsigned long long)cell << (3 * b)) | m;
     vals[i] = i;
     if (bad) atomicOr((unsigned long long*)&ctr->err, 1ull);
 }
 
 __global__ void __launch_bounds__(256) k_cell_bounds(const unsigned long long* __restrict__ keys, int n,
-                                                     int shift, int total_cells, int* __restrict__ cell_start) {
+                                                     int shift, int total_cells, int* __restrict__ cell_start,
+                                                     unsigned long long* check) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p > n) return;
     const int c_prev = p > 0 ? (int)(keys[p - 1] >> shift) : -1;
     const int c_cur = p < n ? (int)(keys[p] >> shift) : total_cells;
+    if (!SR_BOUND(c_prev >= -1 && c_cur <= total_cells, check, kChkCellBounds)) return;
     for (int c = c_prev + 1; c <= c_cur; ++c) cell_start[c] = p;
 }
 
@@ -189,13 +193,15 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
     const int* __restrict__ ccs, const int* __restrict__ chunk_cell, int total_cells,
     const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base, int n_vol,
     float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
-    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, const unsigned char* __restrict__ active) {
+    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, const unsigned char* __restrict__ active,
+    int n, long long max_chunks, unsigned long long* check) {
     constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
     const int n_chunks = ccs[total_cells];
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_chunks; k += warps) {
         const int cell = chunk_cell[k];
+        if (!SR_BOUND(k < max_chunks && cell >= 0 && cell < total_cells, check, kChkChunkFill)) continue;
         const int r0 = (k - ccs[cell]) * C;
         const int n_cell = cell_start[cell + 1] - cell_start[cell];
         const int v = n_vol > 1 ? volume_of_cell(cell, vol_cell_base, n_vol) : 0;
@@ -213,8 +219,10 @@ __global__ void __launch_bounds__(256) k_chunk_fill(
             orig[s] = -1;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) { q[s][ax] = 0; t[s][ax] = 0.0; F[s][ax] = -1; mant[s][ax] = 0ull; }
+            if (valid[s] && !SR_BOUND(cell_start[cell] + rank < n, check, kChkChunkFill)) valid[s] = false;
             if (valid[s]) {
                 orig[s] = perm[cell_start[cell] + rank];
+                if (!SR_BOUND(orig[s] >= 0 && orig[s] < n, check, kChkChunkFill)) orig[s] = 0;
                 const double x3[3] = {pos[3ll * orig[s]], pos[3ll * orig[s] + 1], pos[3ll * orig[s] + 2]};
                 // the integer path needs t >= 1 on every axis for the offsets;
                 // q holds the unclamped floor(t) there (the anchor is clamped)
@@ -290,11 +298,12 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, cons
         SR_LAUNCH_CHECK("k_keys");
     }
     int which = 0;
-    int rc = radix_sort_pairs(p->keys, p->vals, ni, p->key_bits, p->rs_particles, st, &which);
+    int rc = radix_sort_pairs(p->keys, p->vals, ni, p->key_bits, p->rs_particles, st, &which, &p->ctr->check);
     if (rc) return rc;
     p->sorted = which;
     const int tc = (int)p->total_cells;
-    k_cell_bounds<<<(ni + 1 + 255) / 256, 256, 0, st>>>(p->keys[which], ni, 3 * b, tc, p->cell_start);
+    k_cell_bounds<<<(ni + 1 + 255) / 256, 256, 0, st>>>(p->keys[which], ni, 3 * b, tc, p->cell_start,
+                                                        &p->ctr->check);
     SR_LAUNCH_CHECK("k_cell_bounds");
     k_cell_nch<<<(tc + 1 + 255) / 256, 256, 0, st>>>(p->cell_start, tc, 32 * p->chunk_k, p->cell_nch);
     SR_LAUNCH_CHECK("k_cell_nch");
@@ -308,11 +317,13 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, cons
     if (p->chunk_k == 2)
         k_chunk_fill<2><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
                                                 p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
-                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active);
+                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active, ni, p->max_chunks,
+                                                &p->ctr->check);
     else
         k_chunk_fill<1><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
                                                 p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
-                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active);
+                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active, ni, p->max_chunks,
+                                                &p->ctr->check);
     SR_LAUNCH_CHECK("k_chunk_fill");
     return launch_cost_and_order(p, st);
 }

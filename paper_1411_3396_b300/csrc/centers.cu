@@ -48,7 +48,7 @@ struct CtrDev {
     unsigned long long max_members;
     unsigned long long pairs;          // sum N_h (N_h - 1) / 2
     unsigned long long evaluated;      // unordered pair terms the symmetric kernel evaluates
-    unsigned long long reserved;
+    unsigned long long check;          // bounds-checked build: code of the first failed check
 };
 
 typedef unsigned long long f2;
@@ -108,6 +108,7 @@ __global__ void k_ctr_reset(CtrDev* c, long long n) {
     c->max_members = 0;
     c->pairs = 0;
     c->evaluated = 0;
+    c->check = 0;
 }
 
 __global__ void k_ctr_keys(const int* __restrict__ labels, long long n, int nh,
@@ -299,7 +300,7 @@ k_ctr_pairs(const float4* __restrict__ slot_pos, unsigned long long* __restrict_
             const int2* __restrict__ row_tab, const int* __restrict__ row_item0,
             const int* __restrict__ row0, const int* __restrict__ pblk, const int* __restrict__ nblk,
             const int* __restrict__ start, const int* __restrict__ end, int nh, float eps2,
-            float scale, CtrDev* c) {
+            float scale, CtrDev* c, long long slot_max) {
     __shared__ WarpSmem smem[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem& sm = smem[warp];
@@ -330,6 +331,10 @@ k_ctr_pairs(const float4* __restrict__ slot_pos, unsigned long long* __restrict_
         const long long base = (long long)pblk[h] * kBlk;
         const int q0 = kTileRows * t + (item - row_item0[lo]) * kJMax;
         const int q1 = min(q0 + kJMax, nb);
+        // the halo's blocks lie inside the slot arrays, and its members inside its blocks
+        if (!SR_BOUND(base >= 0 && base + (long long)nb * kBlk <= slot_max && cnt <= nb * kBlk && q0 < nb,
+                      &c->check, sr::kChkCenters))
+            continue;
 
         f2 XI[kTileRows], YI[kTileRows], ZI[kTileRows], P[kTileRows];
         long long acc[kTileRows];
@@ -686,7 +691,7 @@ int sr_centers_potential(sr_centers* c, void* stream) {
             SR_LAUNCH_CHECK("k_ctr_queue_reset");
             k_ctr_pairs<<<c->pair_blocks, kThreads, 0, st>>>(c->slot_pos, c->psi, c->row_tab, c->row_item0,
                                                              c->row0, c->pblk, c->nblk, c->start, c->end,
-                                                             nh, c->eps2, scale, c->ctr);
+                                                             nh, c->eps2, scale, c->ctr, c->slot_max);
             SR_LAUNCH_CHECK("k_ctr_pairs");
         } else {
             k_ctr_plain<<<grid_for(n, T), T, 0, st>>>(c->slot_pos, c->psi, c->keys[c->sorted], c->start,
@@ -753,6 +758,7 @@ int sr_centers_get_info(sr_centers* c, sr_centers_info* out) {
     out->variant = c->variant;
     out->bad_labels = (int64_t)h.bad_labels;
     out->wide_members = (int64_t)h.wide;
+    out->check_code = (int64_t)h.check;
     return SR_OK;
 }
 

@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
         it_idx = __shfl_sync(kFull, it_idx, 0);
         if (it_idx >= n_items) break;
         const int I = a.order[it_idx];
+        if (!SR_BOUND(I >= 0 && I < a.ccs[a.total_cells], &a.ctr->check, kChkItem)) continue;
         const Item it = load_item(a, I);
         const VolDev& V = SINGLE ? v0 : a.vols[it.vol];
         const Consts KC = load_consts(V, MODE == kVjp);
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
                 const float gz = fmaxf(fmaxf(zj - it.hi[2], it.lo[2] - zj), 0.f);
                 const bool keep = gx * gx + gy * gy + gz * gz < KC.rcm2;
                 const unsigned m = __ballot_sync(kFull, keep);
-                if (keep) {
+                if (keep && SR_BOUND(w.wr + __popc(m & lt) - w.rd < kRing, &a.ctr->check, kChkRing)) {
                     const int slot = (w.wr + __popc(m & lt)) & (kRing - 1);
                     if (PACKED) {
                         // pair-interleaved ring: entry p -> x, y at float4 p/2 lanes
@@ -342,6 +343,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(const Args a, const 
             // active particles only (slot w = 1; a passive neighbour's row is left untouched)
             if (l < it.cnt && a.slot_pos[(long long)I * C + l].w > 0.f) {
                 const int orig = a.slot_idx[(long long)I * C + l];
+                if (!SR_BOUND(orig >= 0 && orig < a.n_rows, &a.ctr->check, kChkRow)) continue;
                 const float ox = (w.sx[k] - w.cx[k]) * KC.scale;
                 const float oy = (w.sy[k] - w.cy[k]) * KC.scale;
                 const float oz = (w.sz[k] - w.cz[k]) * KC.scale;
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(256) k_cost(const Args a, int max_chunks, unsi
                     int nx = c[0] + ox;
                     nx += nx < 0 ? V.n_c : (nx >= V.n_c ? -V.n_c : 0);
                     const int cell = V.cell_base + (nz * V.n_c + ny) * V.n_c + nx;
+                    if (!SR_BOUND(cell >= 0 && cell < a.total_cells, &a.ctr->check, kChkCell)) continue;
                     sum += (unsigned)(a.cell_start[cell + 1] - a.cell_start[cell]);
                 }
             }
@@ -439,13 +442,14 @@ __global__ void __launch_bounds__(256) k_cost(const Args a, int max_chunks, unsi
 
 __global__ void __launch_bounds__(256) k_gather_g(const float* __restrict__ g, const int* __restrict__ slot_idx,
                                                   const int* __restrict__ ccs, int total_cells, int chunk,
-                                                  float scale, float4* __restrict__ slot_g) {
+                                                  float scale, float4* __restrict__ slot_g, long long n_rows,
+                                                  unsigned long long* check) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n_slots = (long long)ccs[total_cells] * chunk;
     if (s >= n_slots) return;
     const int idx = slot_idx[s];
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (idx >= 0) {
+    if (idx >= 0 && SR_BOUND(idx < n_rows, check, kChkRow)) {
         const float4 x = reinterpret_cast<const float4*>(g)[idx];
         v = make_float4(x.x * scale, x.y * scale, x.z * scale, 0.f);
     }
@@ -548,7 +552,7 @@ int launch_cost_and_order(sr_plan* p, cudaStream_t st) {
     k_cost<<<(int)((mc + 255) / 256), 256, 0, st>>>(a, (int)mc, p->cost, p->lpt_keys[0], p->lpt_vals[0]);
     SR_LAUNCH_CHECK("k_cost");
     int which = 0;
-    int rc = radix_sort_pairs(p->lpt_keys, p->lpt_vals, (int)mc, 8, p->rs_chunks, st, &which);
+    int rc = radix_sort_pairs(p->lpt_keys, p->lpt_vals, (int)mc, 8, p->rs_chunks, st, &which, &p->ctr->check);
     if (rc) return rc;
     p->order = p->lpt_vals[which];
     return SR_OK;
@@ -582,7 +586,7 @@ int launch_vjp(sr_plan* p, const float* g_acc, float* g_pos, float g_scale, int 
     const int C = 32 * p->chunk_k;
     const long long n_slots = p->max_chunks * C;
     k_gather_g<<<(int)((n_slots + 255) / 256), 256, 0, st>>>(g_acc, p->slot_idx, p->ccs, (int)p->total_cells,
-                                                             C, g_scale, p->slot_g);
+                                                             C, g_scale, p->slot_g, p->n_binned, &p->ctr->check);
     SR_LAUNCH_CHECK("k_gather_g");
     Args a = make_args(p);
     a.out = g_pos;

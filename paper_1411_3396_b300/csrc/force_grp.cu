@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
         it_idx = __shfl_sync(kFull, it_idx, 0);
         if (it_idx >= n_items) break;
         const int I = a.order[it_idx];
+        if (!SR_BOUND(I >= 0 && I < a.ccs[a.total_cells], &a.ctr->check, kChkItem)) continue;
         const Item it = load_item(a, I);
         const VolDev& V = SINGLE ? v0 : a.vols[it.vol];
         const Consts KC = load_consts(V, false);
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
                     const float gz = fmaxf(fmaxf(lo.z - e.z, e.z - hi.z), 0.f);
                     const bool in = lane < n && gx * gx + gy * gy + gz * gz < KC.rcm2;
                     const unsigned m = __ballot_sync(kFull, in);
-                    if (in) {
+                    if (in && SR_BOUND(wg[g] + __popc(m & lt) - rg[g] < RING, &a.ctr->check, kChkGroupRing)) {
                         float* A = reinterpret_cast<float*>(gA + g * (RING / 2));
                         float* B = reinterpret_cast<float*>(gB + g * (RING / 2));
                         ring_put(A, B, (wg[g] + __popc(m & lt)) & (RING - 1), e.x, e.y, e.z);
@@ -219,7 +220,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
             const float gz = fmaxf(fmaxf(zj - it.hi[2], it.lo[2] - zj), 0.f);
             const bool keep = gx * gx + gy * gy + gz * gz < KC.rcm2;
             const unsigned m = __ballot_sync(kFull, keep);
-            if (keep) stage[(w1 + __popc(m & lt)) & (kStage - 1)] = make_float4(xj, yj, zj, 0.f);
+            if (keep && SR_BOUND(w1 + __popc(m & lt) - r1 < kStage, &a.ctr->check, kChkGroupRing))
+                stage[(w1 + __popc(m & lt)) & (kStage - 1)] = make_float4(xj, yj, zj, 0.f);
             w1 += __popc(m);
             __syncwarp();
             if (w1 - r1 >= 32) {
@@ -246,8 +248,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
         }
 
         int cpairs = 0;
-        if (valid && pi.w > 0.f) {                                  // active particles only
-            const int orig = a.slot_idx[(long long)I * 32 + lane];
+        const int orig = a.slot_idx[(long long)I * 32 + lane];
+        // active particles only (slot w = 1; a passive neighbour's row is left untouched)
+        if (valid && pi.w > 0.f && SR_BOUND(orig >= 0 && orig < a.n_rows, &a.ctr->check, kChkRow)) {
             const float ox = (sx - cx) * KC.scale;
             const float oy = (sy - cy) * KC.scale;
             const float oz = (sz - cz) * KC.scale;

@@ -92,6 +92,13 @@ int grid_for(long long n) {
     return (int)(g > 0 ? g : 1);
 }
 
+// One thread evaluates a bounds check whose condition is false, with no
+// memory access behind it: exercises the error word of the bounds-checked
+// build and its report by sr_plan_status (the release build records nothing).
+__global__ void k_check_selftest(Counters* ctr) {
+    if (!SR_BOUND(false, &ctr->check, kChkSelfTest)) return;
+}
+
 }  // namespace
 
 int launch_kick(long long n, const float* acc, float* vel, float dt, cudaStream_t st) {
@@ -116,6 +123,12 @@ int launch_invariants(long long n, const float* vel, const float* acc, double* o
     SR_LAUNCH_CHECK("k_inv_partial");
     k_inv_final<<<1, 32, 0, st>>>(partials, kInvBlocks, out);
     SR_LAUNCH_CHECK("k_inv_final");
+    return SR_OK;
+}
+
+int launch_check_selftest(sr_plan* p, cudaStream_t st) {
+    k_check_selftest<<<1, 1, 0, st>>>(p->ctr);
+    SR_LAUNCH_CHECK("k_check_selftest");
     return SR_OK;
 }
 

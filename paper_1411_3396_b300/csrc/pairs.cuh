@@ -37,6 +37,7 @@ struct Args {
     int accumulate;
     float* vel;                       // force: nullable, fused kick vel += acc * kdt
     float kdt;
+    long long n_rows;                 // caller rows of the binning (bounds of slot_idx entries)
 };
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -132,6 +133,7 @@ __device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const It
                 int nx = c[0] + ox, kx = 0;
                 if (nx < 0) { nx += V.n_c; kx = -1; } else if (nx >= V.n_c) { nx -= V.n_c; kx = 1; }
                 const int cell = V.cell_base + (nz * V.n_c + ny) * V.n_c + nx;
+                if (!SR_BOUND(cell >= 0 && cell < a.total_cells, &a.ctr->check, kChkCell)) continue;
                 const int j0 = a.ccs[cell], j1 = a.ccs[cell + 1];
                 const int bx = kx * V.M - it.q[0];
                 const int by = ky * V.M - it.q[1];
@@ -140,7 +142,7 @@ __device__ __forceinline__ void for_each_neighbour_chunk(const Args& a, const It
                     const int J = jb + lane;
                     bool pass = false;
                     float Sx = 0.f, Sy = 0.f, Sz = 0.f;
-                    if (J < j1) {
+                    if (J < j1 && SR_BOUND(J >= 0 && J < a.ccs[a.total_cells], &a.ctr->check, kChkChunk)) {
                         const int4 mj = a.meta[J];
                         const float4 lj = a.clo[J];
                         const float4 hj = a.chi[J];
@@ -208,8 +210,10 @@ __device__ __forceinline__ void for_each_neighbour_chunk_flat(const Args& a, con
         if (ny < 0) { ny += V.n_c; ky = -1; } else if (ny >= V.n_c) { ny -= V.n_c; ky = 1; }
         if (nz < 0) { nz += V.n_c; kz = -1; } else if (nz >= V.n_c) { nz -= V.n_c; kz = 1; }
         const int cell = V.cell_base + (nz * V.n_c + ny) * V.n_c + nx;
-        j0 = a.ccs[cell];
-        cnt = a.ccs[cell + 1] - j0;
+        if (SR_BOUND(cell >= 0 && cell < a.total_cells, &a.ctr->check, kChkCell)) {
+            j0 = a.ccs[cell];
+            cnt = a.ccs[cell + 1] - j0;
+        }
         bx = kx * V.M - it.q[0];
         by = ky * V.M - it.q[1];
         bz = kz * V.M - it.q[2];
@@ -268,6 +272,8 @@ __device__ __forceinline__ void for_each_neighbour_chunk_flat(const Args& a, con
         float Sx = 0.f, Sy = 0.f, Sz = 0.f;
         if (t < total) {
             J = jk + (t - ek);
+        }
+        if (t < total && SR_BOUND(J >= 0 && J < a.ccs[a.total_cells], &a.ctr->check, kChkChunk)) {
             const int4 mj = a.meta[J];
             const float4 lj = a.clo[J];
             const float4 hj = a.chi[J];
@@ -280,7 +286,8 @@ __device__ __forceinline__ void for_each_neighbour_chunk_flat(const Args& a, con
             pass = gx * gx + gy * gy + gz * gz < V.rcm2u;
         }
         const unsigned m = __ballot_sync(kFull, pass);
-        if (pass) list[n + __popc(m & lt)] = make_int4(J, __float_as_int(Sx), __float_as_int(Sy), __float_as_int(Sz));
+        if (pass && SR_BOUND(n + __popc(m & lt) < CAP, &a.ctr->check, kChkList))
+            list[n + __popc(m & lt)] = make_int4(J, __float_as_int(Sx), __float_as_int(Sy), __float_as_int(Sz));
         n += __popc(m);
         if (n > CAP - 32) visit_list();
     }
@@ -484,6 +491,7 @@ inline Args make_args(sr_plan* p) {
     a.vols = p->vols;
     a.order = p->order;
     a.ctr = p->ctr;
+    a.n_rows = p->n_binned;
     return a;
 }
 

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_hist(const unsigned long
 __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
     const unsigned long long* __restrict__ kin, const int* __restrict__ vin,
     unsigned long long* __restrict__ kout, int* __restrict__ vout, int n, int shift,
-    const int* __restrict__ hist_scan, int n_tiles) {
+    const int* __restrict__ hist_scan, int n_tiles, unsigned long long* check) {
     constexpr int kWarps = kScanThreads / 32;
     __shared__ int wh[kWarps][kRadixBuckets];
     __shared__ int gbase[kRadixBuckets];
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
         const unsigned long long k = skey[t];
         const int dd = (int)((k >> shift) & (kRadixBuckets - 1));
         const int pos = gbase[dd] + (t - loff[dd]);
+        if (!SR_BOUND(pos >= 0 && pos < n, check, kChkScatter)) continue;
         kout[pos] = k;
         vout[pos] = sval[t];
     }
@@ -238,7 +239,7 @@ void radix_free(RadixScratch& r) {
 }
 
 int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_bits,
-                     RadixScratch& r, cudaStream_t st, int* which) {
+                     RadixScratch& r, cudaStream_t st, int* which, unsigned long long* check) {
     int cur = 0;
     *which = 0;
     if (n <= 0) return SR_OK;
@@ -251,7 +252,7 @@ int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_b
         int rc = exclusive_scan(r.hist, r.hist_scan, hn, r.scan, st);
         if (rc) return rc;
         k_radix_scatter<<<t, kScanThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n,
-                                                    shift, r.hist_scan, t);
+                                                    shift, r.hist_scan, t, check);
         SR_LAUNCH_CHECK("k_radix_scatter");
         cur = 1 - cur;
     }

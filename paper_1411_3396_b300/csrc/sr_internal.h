@@ -12,6 +12,39 @@
 namespace sr {
 
 constexpr int kMaxChunkK = 2;       // chunks hold 32 K particles, K = 1 or 2 (K per lane)
+
+// Checks of the bounds-checked build (compiled with -DSR_CHECK): the code
+// a failed check records in its error word.
+enum CheckCode : int {
+    kChkItem = 1,         // pair kernels: work item outside the chunk table
+    kChkCell = 2,         // neighbour cell outside the cell table
+    kChkChunk = 3,        // neighbour chunk outside the chunk table
+    kChkRing = 4,         // pair kernel: staging ring over-filled
+    kChkList = 5,         // flat enumeration: neighbour-chunk list over-filled
+    kChkRow = 6,          // caller row of a slot outside [0, n)
+    kChkGroupRing = 7,    // grouped kernel: staging or group ring over-filled
+    kChkKeyCell = 8,      // binning: cell of a key outside the cell table
+    kChkCellBounds = 9,   // binning: cell-start entry outside the cell table
+    kChkChunkFill = 10,   // binning: sorted position, caller row or slot outside its array
+    kChkScatter = 11,     // radix scatter: destination outside [0, n)
+    kChkCenters = 12,     // center finder: slot or accumulator outside its halo's block
+    kChkSelfTest = 99,    // sr_check_selftest
+};
+
+#ifdef __CUDACC__
+#ifdef SR_CHECK
+// A failed check records its code in *word (the first failure is kept) and
+// yields false, so that the caller skips the access; nothing traps.
+__device__ __forceinline__ bool check_bound(bool ok, unsigned long long* word, int code) {
+    if (!ok && word) atomicCAS(word, 0ull, (unsigned long long)code);
+    return ok;
+}
+#define SR_BOUND(cond, word, code) (sr::check_bound((cond), (word), (code)))
+#else
+// The release build evaluates nothing: the condition is not compiled.
+#define SR_BOUND(cond, word, code) (true)
+#endif
+#endif
 constexpr float kPad = 1.0e30f;     // coordinate of an empty slot: never within r_c
 
 #ifdef __CUDACC__
@@ -137,7 +170,8 @@ struct Counters {
     unsigned long long evals;         // counting variant: candidate (i, j) evaluations, valid i only
     unsigned long long lane_evals;    // counting variant: candidate evaluations x 32 lanes
     long long n_items;                // work items of the pair kernels: chunks holding an active particle
-    long long reserved[2];
+    unsigned long long check;         // bounds-checked build: code of the first failed check (0 = none)
+    long long reserved;
 };
 
 struct ScanScratch {
@@ -248,7 +282,7 @@ void radix_free(RadixScratch& r);
 // Sorts (keys[0], vals[0]) stably by the low key_bits bits; returns in *which
 // the index (0/1) of the buffer pair that holds the result.
 int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_bits,
-                     RadixScratch& r, cudaStream_t st, int* which);
+                     RadixScratch& r, cudaStream_t st, int* which, unsigned long long* check = nullptr);
 
 // binning (bin.cu)
 int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st,
@@ -276,5 +310,6 @@ int launch_drift(sr_plan* p, double* pos, const float* vel, double dt, long long
 int launch_invariants(long long n, const float* vel, const float* acc, double* out,
                       double* partials, cudaStream_t st);
 constexpr int kInvBlocks = 1184;   // 8 * 148
+int launch_check_selftest(sr_plan* p, cudaStream_t st);
 
 }  // namespace sr

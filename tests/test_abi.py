@@ -40,6 +40,16 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_the_same_boundary(lib):
+    # the bounds-checked build (-DSR_CHECK) is the same library with the
+    # index checks compiled in
+    from paper_1411_3396_b300.build import LIB_CHECKED
+    chk = ctypes.CDLL(str(LIB_CHECKED))
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+    assert chk.sr_build_checked() == 1 and lib.sr_build_checked() == 0
+
+
 @pytest.mark.parametrize("mode,mname", [(0, "constrained"), (1, "unconstrained")])
 @pytest.mark.parametrize("rc,sigma,eps", [(3.0, 0.8, 0.1), (3.0, 0.8, 0.05), (2.5, 0.6, 0.02)])
 def test_library_fit_matches_oracle(lib, mode, mname, rc, sigma, eps):

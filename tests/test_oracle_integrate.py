@@ -65,6 +65,23 @@ def test_trajectory_conserves_momentum(coef):
         assert np.all(np.abs(v.sum(axis=0) - p0) < 1e-12 * (1 + np.abs(v).sum()))
 
 
+def test_force_vjp_term_magnitudes(coef):
+    # the per-row magnitude sums bound the sum (triangle inequality), equal
+    # it for a row with one term (an isolated pair: each row holds the same
+    # single term), and the value returned with them is the plain VJP's
+    L = 10.0
+    pos = gen.uniform_box(200, L, 13)
+    gbar = np.random.default_rng(4).standard_normal((200, 3))
+    out, mag = integrate.force_vjp(pos, L, RC, EPS, coef, gbar, absolute=True)
+    np.testing.assert_array_equal(out, integrate.force_vjp(pos, L, RC, EPS, coef, gbar))
+    assert np.all(np.abs(out) <= mag * (1 + 1e-12) + 1e-300)
+    two = gen.two_body(1.7, 20.0, axis=0)
+    g2 = np.array([[0.3, -0.2, 0.5], [-0.1, 0.4, 0.2]])
+    o2, m2 = integrate.force_vjp(two, 20.0, RC, EPS, coef, g2, absolute=True)
+    np.testing.assert_allclose(np.abs(o2), m2, rtol=1e-14)
+    assert np.all(m2 > 0)
+
+
 def test_kick_drift_basic():
     v = integrate.kick(np.ones((2, 3)), np.full((2, 3), 2.0), 0.5)
     np.testing.assert_array_equal(v, 2.0)
