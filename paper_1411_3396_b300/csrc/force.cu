@@ -35,6 +35,7 @@ constexpr int kRing = 256;        // per-warp ring of staged neighbours (packed 
 constexpr int kList = 64;         // per-warp list of neighbour chunks (flat enumeration, FLAGS bit 3)
 constexpr int kVjpMinBlocks = 1;   // VJP kernel: 256-thread blocks, at least this many per SM
 constexpr int vjp_flags(int k) { return k == 1 ? 2 : 0; }   // packed loop for 32-particle chunks
+constexpr int kVjpFlat = 8;        // VJP with the flat neighbour enumeration (FLAGS bit 3)
 
 // Per-lane state: K active particles.
 template <int MODE, int K>
@@ -524,11 +525,21 @@ void launch_mode(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
 
 // The VJP kernel: packed f32x2 pair loop for 32-particle chunks, the scalar
 // loop for 64-particle chunks.
+// The VJP follows the neighbour enumeration of the selected force variant:
+// the flat one when the autotuner (or the caller) chose a flat or grouped
+// variant, i.e. at low density; the same chunks in the same order either
+// way, so the results are the same bits.
 template <int K>
 void launch_vjp(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
     const VolDev& v0 = p->vols_h[0];
-    if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), true><<<blocks, kThreads, 0, st>>>(a, v0);
-    else k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), false><<<blocks, kThreads, 0, st>>>(a, v0);
+    const bool flat = K == 1 && p->variant >= 13;
+    if (flat) {
+        if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K) | kVjpFlat, true><<<blocks, kThreads, 0, st>>>(a, v0);
+        else k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K) | kVjpFlat, false><<<blocks, kThreads, 0, st>>>(a, v0);
+    } else {
+        if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), true><<<blocks, kThreads, 0, st>>>(a, v0);
+        else k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), false><<<blocks, kThreads, 0, st>>>(a, v0);
+    }
 }
 
 }  // namespace

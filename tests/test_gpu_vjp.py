@@ -57,6 +57,23 @@ def test_vjp_on_a_batch_plan(chunk):
         off += n
 
 
+@pytest.mark.parametrize("name", ["diff64", "clustered256"])
+def test_vjp_flat_enumeration_same_bits(name):
+    # the VJP follows the selected force variant's neighbour enumeration,
+    # flat (variants 13-16) or cell by cell: the same chunks in the same
+    # order, so the same bits
+    w = wc.make_workload(wc.small_variant(name))
+    (pos, box), = w["volumes"]
+    plan = make_plan(w["volumes"], w["params"])
+    plan.bin(torch.from_numpy(pos).cuda())
+    g = torch.from_numpy(_g(len(pos), 5)).cuda()
+    plan.set_variant(11)
+    a = to_np(plan.vjp(g))
+    for v in (14, 15):
+        plan.set_variant(v)
+        assert to_np(plan.vjp(g)).tobytes() == a.tobytes(), f"variant {v}"
+
+
 def test_vjp_scale_and_accumulate():
     w = wc.make_workload(wc.small_variant("uniform4k"))
     (pos, box), = w["volumes"]
