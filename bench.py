@@ -416,9 +416,13 @@ def run_ours(args, rank, world, local_rank):
     if batch:
         plan = Plan.batch([b for _, b in vols], [len(p) for p, _ in vols], prm["rc"], prm["eps"], prm["sigma"],
                           sub_bits=args.sub_bits, chunk_size=args.chunk_size)
+    elif args.tune_geometry and world == 1:
+        plan, tune_geometry = Plan.tune(box, prm["rc"], prm["eps"], prm["sigma"], x, reps=1, sub_bits=args.sub_bits)
     else:
         plan = Plan(box, prm["rc"], prm["eps"], prm["sigma"], n, n_cells=args.n_cells, sub_bits=args.sub_bits,
                     chunk_size=args.chunk_size)
+    if not (args.tune_geometry and world == 1 and not batch):
+        tune_geometry = None
     dt = prm["dt"]
     graph_stream = torch.cuda.Stream() if batch else None
     slabbed = world > 1 and not batch
@@ -477,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
     tune_ms = None
     if args.variant >= 0:
         plan.set_variant(args.variant)
-    elif not args.no_autotune:
+    elif not args.no_autotune and tune_geometry is None:
         tune_ms = plan.autotune(reps=1)
     _, pairs_t, _ = plan.force(acc_loc[:len(xl)] if slabbed else acc, count=True)   # slabs: owned rows' pairs
     torch.cuda.synchronize()
@@ -592,7 +596,8 @@ def run_ours(args, rank, world, local_rank):
                    "graph": bool(batch), "r_c": prm["rc"],
                    "eps": prm["eps"], "sigma": prm["sigma"], "dt": dt, "pairs_per_step": pairs,
                    "n_chunks": info["n_chunks"], "workers": info["workers"],
-                   "variant": info["variant"], "autotune_ms": tune_ms, "chunk_size": info["chunk_size"],
+                   "variant": info["variant"], "autotune_ms": tune_ms, "tune_geometry": tune_geometry,
+                   "chunk_size": info["chunk_size"],
                    "sub_bits": info["sub_bits"], "n_cells": plan.volume(0)["n_cells"],
                    "in_range_fraction": pairs / max(evals, 1),
                    "lane_fill": evals / max(lane_evals, 1),
@@ -1525,6 +1530,8 @@ def main():
                     help="diff64: one plan for every substep (binned again in the backward sweep)")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-geometry", action="store_true",
+                    help="single volume: choose chunk size and cells per axis by timing as well (sr_plan_tune)")
     ap.add_argument("--variant", type=int, default=-1, help="force a pair-kernel variant (skips autotuning)")
     ap.add_argument("--chunk-size", type=int, default=0, help="particles per chunk: 32 or 64 (0 = library default)")
     ap.add_argument("--n-cells", type=int, default=0, help="cells per axis (0 = library default)")

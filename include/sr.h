@@ -394,6 +394,34 @@ int sr_plan_set_variant(sr_plan* plan, int variant);
 /* sr_variant_count -- the number of pair-kernel variants (17: 0..16). */
 int sr_variant_count(void);
 
+/* One candidate geometry timed by sr_plan_tune. */
+typedef struct sr_tune_entry {
+    int32_t chunk_size;    /* particles per chunk (the i-tile of the 32-lane kernels)   */
+    int32_t n_cells;       /* cells per axis                                          */
+    int32_t variant;       /* the fastest pair-kernel variant on this geometry         */
+    float ms;              /* its mean time per launch (ms)                            */
+} sr_tune_entry;
+
+/*
+ * sr_plan_tune -- per-plan autotuner over the tile shape and the cell
+ * geometry, then the kernel variant (Sec. 2.1 sizes the blocks to the
+ * load; here the sizes are chosen by timing).  Candidates: chunk size 32
+ * or 64, and cells per axis: the automatic count, and counts giving about
+ * 3/4 and 4/3 of its cell side where the side stays above r_c.  For each,
+ * a plan for n_max particles is created, pos (device, n rows of binary64
+ * x, y, z) binned, and every pair-kernel variant timed (sr_autotune, reps
+ * launches each); the plan of the fastest candidate is returned in *out,
+ * the others are destroyed.  params->n_cells and params->chunk_size are
+ * ignored (the candidates set them).  One volume only.
+ * entries: host array of at least 6 (nullable), receives each candidate's
+ * geometry, best variant and time; *n_entries (nullable) their count.
+ * A set-up call: it allocates, synchronises, and must not be captured.
+ * Errors: as sr_plan_create and sr_bin; SR_ERR_ARG (null out or pos,
+ * reps < 1).
+ */
+int sr_plan_tune(const sr_params* params, int64_t n_max, const double* pos, int64_t n, int reps,
+                 sr_plan** out, sr_tune_entry* entries, int* n_entries, void* stream);
+
 /*
  * sr_autotune -- time each pair-kernel variant on the data of the last
  * sr_bin (reps launches each, CUDA events on stream, synchronising) and

@@ -31,6 +31,11 @@ class SrPlanInfo(ctypes.Structure):
                 ("coef", c_double * 6)]
 
 
+class SrTuneEntry(ctypes.Structure):
+    _fields_ = [("chunk_size", ctypes.c_int32), ("n_cells", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("ms", c_float)]
+
+
 class SrCentersInfo(ctypes.Structure):
     _fields_ = [("n_particles", c_int64), ("n_members", c_int64), ("n_halos", c_int64),
                 ("max_members", c_int64), ("pairs", c_int64), ("items", c_int64),
@@ -75,6 +80,8 @@ SIGNATURES = {
     "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
     "sr_bin_active": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "sr_variant_count": (c_int, []),
+    "sr_plan_tune": (c_int, [POINTER(SrParams), c_int64, c_void_p, c_int64, c_int, POINTER(c_void_p),
+                             POINTER(SrTuneEntry), POINTER(c_int), c_void_p]),
     "sr_build_checked": (c_int, []),
     "sr_check_selftest": (c_int, [c_void_p, c_void_p]),
     "sr_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),

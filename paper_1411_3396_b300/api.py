@@ -87,6 +87,33 @@ class Plan:
         self.binnings = 0           # calls that replaced the plan's binning
 
     @classmethod
+    def tune(cls, box: float, r_c: float, eps: float, sigma: float, pos: torch.Tensor, n_max: int | None = None,
+             reps: int = 1, fit_mode: str = "constrained", sub_bits: int = 0):
+        """A plan whose chunk size, cell count and kernel variant are chosen by
+        timing on pos (sr_plan_tune); returns (plan, candidates), each
+        candidate a dict of chunk_size, n_cells, variant, ms.  The plan is
+        binned on pos."""
+        lib = load()
+        _need(pos, torch.float64, 3, "pos")
+        n = pos.shape[0]
+        n_max = int(n_max or n)
+        prm = _params(box, r_c, eps, sigma, fit_mode, 0, sub_bits, 0)
+        ents = (_lib.SrTuneEntry * 8)()
+        cnt = c_int(0)
+        handle = c_void_p()
+        check(lib.sr_plan_tune(byref(prm), n_max, _ptr(pos), n, int(reps), byref(handle), ents, byref(cnt),
+                               _stream()))
+        plan = cls.__new__(cls)
+        plan._h = handle
+        plan.volume_counts = [n_max]
+        plan.r_c, plan.eps, plan.sigma = float(r_c), float(eps), float(sigma)
+        plan.capacity = n_max
+        plan.n = n
+        plan.binnings = 1
+        cands = [{k: getattr(ents[i], k) for k, _ in _lib.SrTuneEntry._fields_} for i in range(cnt.value)]
+        return plan, cands
+
+    @classmethod
     def batch(cls, boxes, counts, r_c, eps, sigma, fit_mode="constrained", n_cells=None,
               sub_bits=0, chunk_size=0):
         cells = n_cells if n_cells is not None else [0] * len(boxes)

@@ -1,5 +1,6 @@
 // C ABI: plan lifecycle, argument checking, error reporting and the thin
 // wrappers that enqueue the kernels of bin.cu, force.cu, plain.cu, kick.cu.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -588,6 +589,66 @@ int sr_autotune(sr_plan* p, float* acc, int reps, float* ms_out, void* stream) {
     p->variant = best_v;
     p->force_blocks = p->force_blocks_v[best_v];
     return rc;
+}
+
+int sr_plan_tune(const sr_params* params, int64_t n_max, const double* pos, int64_t n, int reps, sr_plan** out,
+                 sr_tune_entry* entries, int* n_entries, void* stream) {
+    if (!out) return set_error(SR_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (n_entries) *n_entries = 0;
+    if (!params || (!pos && n > 0) || reps < 1) return set_error(SR_ERR_ARG, "null params or pos, or reps < 1");
+    if (n < 1 || n > n_max) return set_error(SR_ERR_CAPACITY, "n must be in [1, n_max]");
+    int rc = check_physics(*params);
+    if (rc) return rc;
+    const double min_side = params->r_c * kSideMargin;
+    const double target = min_side > 4.0 ? min_side : 4.0;
+    const int nc0 = std::max(1, (int)std::floor(params->box / target));
+    std::vector<int> cells;
+    for (int nc : {nc0, (int)std::floor(nc0 * 4.0 / 3.0), (int)std::floor(nc0 * 3.0 / 4.0)}) {
+        if (nc < 1 || params->box / nc < min_side) continue;
+        if (std::find(cells.begin(), cells.end(), nc) == cells.end()) cells.push_back(nc);
+    }
+    float* acc = nullptr;
+    cudaError_t e = cudaMalloc(&acc, sizeof(float) * 4 * (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(e, "sr_plan_tune scratch");
+    std::vector<float> ms(kVariants);
+    sr_plan* best = nullptr;
+    float best_ms = 1e30f;
+    int k = 0;
+    for (int chunk : {32, 64}) {
+        for (int nc : cells) {
+            sr_params q = *params;
+            q.chunk_size = chunk;
+            q.n_cells = nc;
+            sr_plan* p = nullptr;
+            rc = sr_plan_create(&q, n_max, &p);
+            if (!rc) rc = sr_bin(p, pos, n, stream);
+            if (!rc) rc = sr_autotune(p, acc, reps, ms.data(), stream);
+            if (rc) {
+                if (p) sr_plan_destroy(p);
+                break;
+            }
+            const float t = ms[p->variant];
+            if (entries) entries[k] = sr_tune_entry{chunk, nc, p->variant, t};
+            ++k;
+            if (t < best_ms) {
+                if (best) sr_plan_destroy(best);
+                best = p;
+                best_ms = t;
+            } else {
+                sr_plan_destroy(p);
+            }
+        }
+        if (rc) break;
+    }
+    cudaFree(acc);
+    if (n_entries) *n_entries = k;
+    if (rc) {
+        if (best) sr_plan_destroy(best);
+        return rc;
+    }
+    *out = best;
+    return SR_OK;
 }
 
 int sr_graph_capture(sr_plan* p, const double* pos, float* vel, float* acc, float dt, int64_t n, void* stream) {

@@ -170,6 +170,25 @@ def test_grouped_variants_brute_force_tiny_boxes():
             assert abs(int(pairs.item()) - int(cnt.sum())) <= 8
 
 
+@pytest.mark.parametrize("name", ["zeldovich128", "clustered256"])
+def test_geometry_tuner_plan_matches_oracle(name):
+    # sr_plan_tune: chunk size, cells per axis and variant chosen by timing;
+    # the kept plan is the fastest candidate and its forces meet the bar
+    from paper_1411_3396_b300 import Plan
+    w = _work(name)
+    (pos, box), = w["volumes"]
+    prm = w["params"]
+    plan, cands = Plan.tune(box, prm["rc"], prm["eps"], prm["sigma"], torch.from_numpy(pos).cuda())
+    assert len(cands) >= 4 and {c["chunk_size"] for c in cands} == {32, 64}
+    info = plan.info()
+    best = min(cands, key=lambda c: c["ms"])
+    assert (info["chunk_size"], plan.volume(0)["n_cells"], info["variant"]) == \
+        (best["chunk_size"], best["n_cells"], best["variant"])
+    a_ref, _ = oracle_force(w["volumes"], prm)
+    assert_force_close(to_np(plan.force()), a_ref, f"{name} tuned geometry")
+    plan.close()
+
+
 def test_plain_kernel_matches_oracle(small_case):
     name, w, chunk = small_case
     pos = np.concatenate([p for p, _ in w["volumes"]])
