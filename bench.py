@@ -424,8 +424,9 @@ def run_ours(args, rank, world, local_rank):
     if not (args.tune_geometry and world == 1 and not batch):
         tune_geometry = None
     dt = prm["dt"]
-    graph_stream = torch.cuda.Stream() if batch else None
     slabbed = world > 1 and not batch
+    graphed = not slabbed            # bin + force with the fused kick replayed as one captured CUDA graph
+    graph_stream = torch.cuda.Stream() if graphed else None
     if slabbed:
         # overload slab decomposition of the one volume: every rank keeps the
         # particles of its slab of cells (in id order) and, each step,
@@ -456,8 +457,8 @@ def run_ours(args, rank, world, local_rank):
             slab_step(slabs, x_own, ids_own, acc_loc, vel_loc, slab_force_kick)
             plan.invariants(vel_loc[:n_own], acc_loc[:n_own], inv)
             return
-        if batch:
-            # one captured graph: bin + persistent force + kick over all volumes
+        if graphed:
+            # one captured graph: bin + persistent force + kick (over all volumes of a batch)
             if ev is not None:
                 ev[0].record()
             plan.graph_launch()
@@ -490,7 +491,7 @@ def run_ours(args, rank, world, local_rank):
     ctr = plan.export("counters").cpu().numpy()
     evals, lane_evals = int(ctr[3]), int(ctr[4])
 
-    if batch:
+    if graphed:
         torch.cuda.set_stream(graph_stream)
         plan.graph_capture(x, vel, acc, dt)
     for _ in range(args.warmup):
@@ -523,7 +524,7 @@ def run_ours(args, rank, world, local_rank):
     pairs_all, ms_max = reduce_over_ranks(pairs, ms, world, dev)
     value = pairs_all / (ms_max * 1e-3)
     graph_ms = None
-    if batch:
+    if graphed:
         # the timed step is the captured graph (bin + pair kernel + kick);
         # the pair kernel itself is timed on the graph's binning, on the
         # same stream, with the kick applied to a scratch copy of vel
@@ -593,7 +594,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": n, "volumes": len(vols),
                    "box": box if not batch else [min(b for _, b in vols), max(b for _, b in vols)],
-                   "graph": bool(batch), "r_c": prm["rc"],
+                   "graph": bool(graphed), "r_c": prm["rc"],
                    "eps": prm["eps"], "sigma": prm["sigma"], "dt": dt, "pairs_per_step": pairs,
                    "n_chunks": info["n_chunks"], "workers": info["workers"],
                    "variant": info["variant"], "autotune_ms": tune_ms, "tune_geometry": tune_geometry,
@@ -914,6 +915,20 @@ def run_pm(args, rank, world, local_rank):
     # fixed-point counters read and written once)
     dep_bytes = 24 * n + 16 * ng ** 3
     dep_gbs = dep_bytes / (phases["deposit_ms"] * 1e-3) / 1e9
+    # the same deposit over a short-range binning's cell order (as in the
+    # force-split step, where the binning is there anyway): timed alone
+    from paper_1411_3396_b300 import Plan
+    bplan = Plan(box, 3.0, 0.05, sigma, n)
+    bplan.bin(x)
+    pm.deposit(x, transform=False, plan=bplan)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        pm.deposit(x, transform=False, plan=bplan)
+    e1.record()
+    torch.cuda.synchronize()
+    dep_binned_ms = e0.elapsed_time(e1) / reps
+    bplan.close()
 
     e2e = None
     if not args.no_e2e:
@@ -951,7 +966,12 @@ def run_pm(args, rank, world, local_rank):
                      "kernel_ms": phases["deposit_ms"], "bytes_per_launch": dep_bytes,
                      "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "fft_pass": {"achieved": fft_gbs, "frac": fft_gbs / hbm, "kernel_ms": pass_ms,
-                                  "bytes_per_launch": pass_bytes, "kernel": "k_fft_pass (one axis)"}},
+                                  "bytes_per_launch": pass_bytes, "kernel": "k_fft_pass (one axis)"},
+                     "deposit_binned": {"kernel": "k_cic_deposit_bricks (over a short-range binning's cell "
+                                                  "order, on-chip tiles; same counts bit for bit)",
+                                        "kernel_ms": dep_binned_ms,
+                                        "achieved": dep_bytes / (dep_binned_ms * 1e-3) / 1e9,
+                                        "frac": dep_bytes / (dep_binned_ms * 1e-3) / 1e9 / hbm}},
         "e2e": e2e,
         "gpu_launches": int(l1 - l0),
         "clocks": clocks,
@@ -1153,7 +1173,7 @@ def run_step(args, rank, world, local_rank):
         plan.force(acc)
         if ev is not None:
             ev[1].record()
-        pm.deposit(x)
+        pm.deposit(x, plan=plan)                   # over the short-range binning's cell order
         pk = pm.power()
         pm.force(x, acc, accumulate=True)
         if ev is not None:

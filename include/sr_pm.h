@@ -69,6 +69,22 @@ int sr_pm_destroy(sr_pm* pm);
 int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream);
 
 /*
+ * sr_pm_deposit_binned -- the same CIC counts, bit for bit, computed over
+ * the cell order of a one-volume short-range plan that binned these n
+ * positions with the same box (Sec. 2: both halves of the force split read
+ * the same particles; the short-range binning is reused).  Each block
+ * deposits a brick of cells into a shared-memory tile first and then adds
+ * the tile to the mesh, so most of the 8 atomics per particle stay on chip.
+ * pos: device, the n rows the plan binned (caller order).  If the plan's
+ * cells hold too many mesh points for a tile, this falls back to
+ * sr_pm_deposit.
+ * Errors: SR_ERR_ARG (null argument, a batch plan, n different from the
+ * plan's binning, another box), SR_ERR_STATE (plan not binned),
+ * SR_ERR_CAPACITY (n > n_max).
+ */
+int sr_pm_deposit_binned(sr_pm* pm, const sr_plan* plan, const double* pos, int64_t n, void* stream);
+
+/*
  * sr_pm_transform -- delta of the last deposit and its forward FFT, the
  * input of sr_pm_power and sr_pm_force.  Errors: SR_ERR_STATE before a
  * deposit.

@@ -99,6 +99,7 @@ SIGNATURES = {
     "sr_pm_create": (c_int, [c_int, c_double, c_double, c_int64, POINTER(c_void_p)]),
     "sr_pm_destroy": (c_int, [c_void_p]),
     "sr_pm_deposit": (c_int, [c_void_p, c_void_p, c_int64, c_void_p]),
+    "sr_pm_deposit_binned": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "sr_pm_transform": (c_int, [c_void_p, c_void_p]),
     "sr_pm_power": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sr_pm_force": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]),

@@ -42,11 +42,16 @@ class PM:
         except Exception:
             pass
 
-    def deposit(self, pos: torch.Tensor, transform: bool = True):
+    def deposit(self, pos: torch.Tensor, transform: bool = True, plan=None):
         """CIC counts of pos; with transform, also delta and its FFT (the
-        input of power() and force())."""
+        input of power() and force()).  With plan (a one-volume Plan that
+        binned these positions, same box), the deposit runs over the plan's
+        cell order with on-chip tiles (sr_pm_deposit_binned): the same bits."""
         _check_pos(pos)
-        check(load().sr_pm_deposit(self._h, _ptr(pos), int(pos.shape[0]), _stream()))
+        if plan is None:
+            check(load().sr_pm_deposit(self._h, _ptr(pos), int(pos.shape[0]), _stream()))
+        else:
+            check(load().sr_pm_deposit_binned(self._h, plan._h, _ptr(pos), int(pos.shape[0]), _stream()))
         if transform:
             self.transform()
 

@@ -179,3 +179,45 @@ def test_full_clustered_256_power_and_sampled_forces():
     r = rel_errors(acc[idx, :3].astype(np.float64), ref)
     print(f"256^3: sampled PM accel rel err median {np.median(r):.2e} max {r.max():.2e}")
     assert np.median(r) <= 1e-5 and r.max() <= 1e-4
+
+
+def _binned_vs_plain(pos, box, ng, chunk=32, n_cells=0, sub_bits=0):
+    from paper_1411_3396_b300 import Plan
+    x = torch.from_numpy(pos).cuda()
+    plan = Plan(box, 3.0, 0.1, 0.8, len(pos), n_cells=n_cells, chunk_size=chunk, sub_bits=sub_bits)
+    plan.bin(x)
+    p = _pm(ng, box, 0.8, len(pos))
+    p.deposit(x, transform=False)
+    ref = p.export("counts").cpu().numpy()
+    p.deposit(x, transform=False, plan=plan)
+    got = p.export("counts").cpu().numpy()
+    p.close()
+    plan.close()
+    return got, ref
+
+
+@pytest.mark.parametrize("ng,chunk", [(16, 32), (32, 32), (32, 64), (64, 32)])
+def test_binned_deposit_same_bits(clustered, ng, chunk):
+    # the deposit over the short-range binning's cell order (on-chip tiles
+    # per brick of cells) adds the same integers as the caller-order one
+    pos, box = clustered
+    got, ref = _binned_vs_plain(pos, box, ng, chunk)
+    assert got.tobytes() == ref.tobytes()
+    # unwrapped positions in [-L, 2L) and a mesh that is not a multiple of
+    # the cells (box 20: 5 cells of side 4 against a 16^3 mesh of spacing
+    # 1.25): tiles with margins, corners past them go straight to the grid
+    L = 20.0
+    q, _, _ = gen.nfw_clustered(5000, L, 41, m_lo=40.0, m_hi=900.0)
+    q = q + np.random.default_rng(3).choice([-1.0, 0.0, 1.0], size=q.shape) * L
+    q = np.where(q < -L, q + L, np.where(q >= 2 * L, q - L, q))
+    got, ref = _binned_vs_plain(q, L, 16, chunk)
+    assert got.tobytes() == ref.tobytes()
+    got, ref = _binned_vs_plain(q, L, 16, chunk, n_cells=6)       # cell side 3.33: tiles of 2.67 mesh cells
+    assert got.tobytes() == ref.tobytes()
+
+
+def test_binned_deposit_full_clustered_256():
+    w = wc.make_workload(wc.CONFIGS["clustered256"])
+    (pos, box), = w["volumes"]
+    got, ref = _binned_vs_plain(pos, box, 256)
+    assert got.tobytes() == ref.tobytes()
