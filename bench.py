@@ -967,8 +967,8 @@ def run_pm(args, rank, world, local_rank):
                      "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "fft_pass": {"achieved": fft_gbs, "frac": fft_gbs / hbm, "kernel_ms": pass_ms,
                                   "bytes_per_launch": pass_bytes, "kernel": "k_fft_pass (one axis)"},
-                     "deposit_binned": {"kernel": "k_cic_deposit_bricks (over a short-range binning's cell "
-                                                  "order, on-chip tiles; same counts bit for bit)",
+                     "deposit_binned": {"kernel": "k_cic_deposit_chunks (over a short-range binning's "
+                                                  "chunks, on-chip tiles; same counts bit for bit)",
                                         "kernel_ms": dep_binned_ms,
                                         "achieved": dep_bytes / (dep_binned_ms * 1e-3) / 1e9,
                                         "frac": dep_bytes / (dep_binned_ms * 1e-3) / 1e9 / hbm}},

@@ -72,12 +72,13 @@ int sr_pm_deposit(sr_pm* pm, const double* pos, int64_t n, void* stream);
  * sr_pm_deposit_binned -- the same CIC counts, bit for bit, computed over
  * the cell order of a one-volume short-range plan that binned these n
  * positions with the same box (Sec. 2: both halves of the force split read
- * the same particles; the short-range binning is reused).  Each block
- * deposits a brick of cells into a shared-memory tile first and then adds
- * the tile to the mesh, so most of the 8 atomics per particle stay on chip.
+ * the same particles; the short-range binning is reused).  Each warp
+ * deposits one chunk (at most 32 particles of one binning cell) into a
+ * shared-memory tile of the cell's mesh points first and then adds the
+ * tile to the mesh, so most of the 8 atomics per particle stay on chip.
  * pos: device, the n rows the plan binned (caller order).  If the plan's
  * cells hold too many mesh points for a tile, this falls back to
- * sr_pm_deposit.
+ * sr_pm_deposit (more than 6 mesh cells per binning cell along an axis).
  * Errors: SR_ERR_ARG (null argument, a batch plan, n different from the
  * plan's binning, another box), SR_ERR_STATE (plan not binned),
  * SR_ERR_CAPACITY (n > n_max).

@@ -29,6 +29,7 @@
 #include "sr_internal.h"
 #include "sr_pm.h"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -136,55 +137,75 @@ k_cic_deposit(const double* __restrict__ pos, long long np, double box, double i
     });
 }
 
-// The same deposit over the short-range binning's order (its chunks run
-// cell by cell): one block per brick of S consecutive cells along x of one
-// (y, z) row of cells.  The brick's particles add their corner integers
-// into a shared-memory tile covering the brick's mesh points with a margin
-// (origin one mesh cell below, ratio = mesh cells per binning cell); a
-// corner outside the tile (the binary64 floors of the two grids can put a
-// particle one mesh cell past its binning cell) goes straight to the grid.
-// The tile is then added to the grid, one atomic per nonzero point.
-// Integer sums commute, so the grid is the same bits as k_cic_deposit's;
-// the global atomics drop from 8 per particle to about one per mesh point
-// per brick.
-__global__ void __launch_bounds__(kThreads)
-k_cic_deposit_bricks(const double* __restrict__ pos, const int* __restrict__ ccs,
-                     const int* __restrict__ slot_idx, int chunk, int n_c, int S, double ratio, int wx, int wy,
-                     int wz, double box, double inv_d, int inv_s, int n, float scale,
+// The same deposit over the short-range binning's order: one warp per
+// chunk (at most 32 particles of one binning cell).  The chunk's corners lie
+// in the cell's mesh points plus one layer (ratio = mesh cells per binning
+// cell), so the warp adds them into a shared-memory tile of that region
+// first (at most 32 lanes contend for a point, where the caller-order
+// deposit has every particle of a halo core contend for a few points of the
+// mesh), then adds the tile's nonzero points to the mesh.  A corner outside
+// the tile (the binary64 floors of the two grids can put a particle one mesh
+// cell past its binning cell) goes straight to the mesh.  Integer sums
+// commute: the mesh is the same bits as k_cic_deposit's.
+constexpr int kDepWarps = 8;
+constexpr int kDepTileMax = 512;       // tile points per warp (8 warps: 32 KB)
+
+// 64-bit fixed-point add into a tile point held as two 32-bit words, with
+// native 32-bit shared-memory atomics: the low word's carry is detected from
+// the value it held before the add.  A point's sum stays below 2^64.
+__device__ __forceinline__ void tile_add(unsigned* lo, unsigned* hi, unsigned long long v) {
+    const unsigned vl = (unsigned)v, vh = (unsigned)(v >> 32);
+    const unsigned old = atomicAdd(lo, vl);
+    const unsigned carry = old > 0xffffffffu - vl ? 1u : 0u;
+    if (vh + carry) atomicAdd(hi, vh + carry);
+}
+
+__global__ void __launch_bounds__(kDepWarps * 32)
+k_cic_deposit_chunks(const double* __restrict__ pos, const int* __restrict__ ccs, int total_cells,
+                     const int* __restrict__ chunk_cell, const int* __restrict__ slot_idx, int chunk, int n_c,
+                     double ratio, int wt, double box, double inv_d, int inv_s, int n, float scale,
                      unsigned long long* __restrict__ grid) {
-    extern __shared__ unsigned long long tile[];
-    const int nbx = (n_c + S - 1) / S;
-    const int b = blockIdx.x;
-    const int bx = b % nbx, cy = (b / nbx) % n_c, cz = b / (nbx * n_c);
-    const int cx0 = bx * S, cx1 = min(cx0 + S, n_c);
-    const int x0 = (int)floor(cx0 * ratio) - 1, y0 = (int)floor(cy * ratio) - 1, z0 = (int)floor(cz * ratio) - 1;
-    const int tsize = wx * wy * wz;
-    for (int i = threadIdx.x; i < tsize; i += blockDim.x) tile[i] = 0ull;
-    __syncthreads();
-    const int cell0 = (cz * n_c + cy) * n_c + cx0;
-    const long long s0 = (long long)ccs[cell0] * chunk, s1 = (long long)ccs[cell0 + (cx1 - cx0)] * chunk;
-    for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        const int orig = slot_idx[s];
-        if (orig < 0) continue;                       // empty slot
-        int c[3];
-        float f[3];
-        cic_cell(pos, orig, box, inv_d, inv_s, n, c, f);
-        for_each_cic_corner(c, f, n, scale, [&](int ix, int iy, int iz, unsigned long long v) {
-            int dx = ix - x0, dy = iy - y0, dz = iz - z0;   // in (-n, n + 1): one wrap at most
-            dx += dx < 0 ? n : (dx >= n ? -n : 0);
-            dy += dy < 0 ? n : (dy >= n ? -n : 0);
-            dz += dz < 0 ? n : (dz >= n ? -n : 0);
-            if (dx < wx && dy < wy && dz < wz) atomicAdd(&tile[(dx * wy + dy) * wz + dz], v);
-            else atomicAdd(&grid[((long long)ix * n + iy) * n + iz], v);
-        });
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < tsize; i += blockDim.x) {
-        const unsigned long long v = tile[i];
-        if (!v) continue;
-        const int dz = i % wz, dy = (i / wz) % wy, dx = i / (wy * wz);
-        const int gx = ((x0 + dx) % n + n) % n, gy = ((y0 + dy) % n + n) % n, gz = ((z0 + dz) % n + n) % n;
-        atomicAdd(&grid[((long long)gx * n + gy) * n + gz], v);
+    __shared__ unsigned tlo[kDepWarps][kDepTileMax], thi[kDepWarps][kDepTileMax];
+    unsigned* lo = tlo[threadIdx.x >> 5];
+    unsigned* hi = thi[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int n_chunks = ccs[total_cells];
+    const int tsize = wt * wt * wt;
+    const int warps = gridDim.x * kDepWarps;
+    for (int k = blockIdx.x * kDepWarps + (threadIdx.x >> 5); k < n_chunks; k += warps) {
+        const int cell = chunk_cell[k];
+        const int cx = cell % n_c, cy = (cell / n_c) % n_c, cz = cell / (n_c * n_c);
+        const int x0 = (int)floor(cx * ratio), y0 = (int)floor(cy * ratio), z0 = (int)floor(cz * ratio);
+        for (int i = lane; i < tsize; i += 32) lo[i] = hi[i] = 0u;
+        __syncwarp();
+        for (int l = lane; l < chunk; l += 32) {
+            const int orig = slot_idx[(long long)k * chunk + l];
+            if (orig < 0) continue;                   // empty slot
+            int c[3];
+            float f[3];
+            cic_cell(pos, orig, box, inv_d, inv_s, n, c, f);
+            for_each_cic_corner(c, f, n, scale, [&](int ix, int iy, int iz, unsigned long long v) {
+                int dx = ix - x0, dy = iy - y0, dz = iz - z0;   // in (-n, n]: one wrap at most
+                dx += dx < 0 ? n : (dx >= n ? -n : 0);
+                dy += dy < 0 ? n : (dy >= n ? -n : 0);
+                dz += dz < 0 ? n : (dz >= n ? -n : 0);
+                if (dx < wt && dy < wt && dz < wt) {
+                    const int t = (dx * wt + dy) * wt + dz;
+                    tile_add(&lo[t], &hi[t], v);
+                } else {
+                    atomicAdd(&grid[((long long)ix * n + iy) * n + iz], v);
+                }
+            });
+        }
+        __syncwarp();
+        for (int i = lane; i < tsize; i += 32) {
+            const unsigned long long v = ((unsigned long long)hi[i] << 32) | lo[i];
+            if (!v) continue;
+            const int dz = i % wt, dy = (i / wt) % wt, dx = i / (wt * wt);
+            const int gx = (x0 + dx) % n, gy = (y0 + dy) % n, gz = (z0 + dz) % n;
+            atomicAdd(&grid[((long long)gx * n + gy) * n + gz], v);
+        }
+        __syncwarp();
     }
 }
 
@@ -817,24 +838,22 @@ int sr_pm_deposit_binned(sr_pm* pm, const sr_plan* plan, const double* pos, int6
     if (n > pm->n_max) return sr::set_error(SR_ERR_CAPACITY, "sr_pm_deposit_binned: n above n_max");
     const sr::VolDev& V = plan->vols_h[0];
     if (V.box != pm->box) return sr::set_error(SR_ERR_ARG, "sr_pm_deposit_binned: the plan's box differs");
-    // brick geometry: S cells along x per block, the tile within kTileBytes
-    constexpr int kTileBytes = 48 * 1024;
+    // the tile: a binning cell's mesh points plus one layer per axis
     const int n_c = V.n_c;
     const double ratio = (double)pm->n / (double)n_c;          // mesh cells per binning cell
-    const int wyz = (int)std::ceil(ratio) + 3;
-    int S = n_c;
-    while (S > 0 && (long long)((int)std::ceil(S * ratio) + 3) * wyz * wyz * 8 > kTileBytes) --S;
-    if (S < 1) return sr_pm_deposit(pm, pos, n, stream);        // cells too coarse for a tile
-    const int wx = (int)std::ceil(S * ratio) + 3;
+    const int wt = (int)std::ceil(ratio) + 2;
+    if ((long long)wt * wt * wt > kDepTileMax) return sr_pm_deposit(pm, pos, n, stream);   // cells too coarse
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double scale = std::ldexp(1.0, pm->fixed_shift);
     SR_CUDA_CHECK(cudaMemsetAsync(pm->fx, 0, sizeof(unsigned long long) * (size_t)pm->n3, st));
-    const long long blocks = (long long)n_c * n_c * ((n_c + S - 1) / S);
-    const size_t smem = sizeof(unsigned long long) * (size_t)wx * wyz * wyz;
-    k_cic_deposit_bricks<<<(unsigned)blocks, kThreads, smem, st>>>(
-        pos, plan->ccs, plan->slot_idx, 32 * plan->chunk_k, n_c, S, ratio, wx, wyz, wyz, pm->box,
-        pm->n / pm->box, mesh_exp(pm), pm->n, (float)scale, pm->fx);
-    SR_LAUNCH_CHECK("k_cic_deposit_bricks");
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (plan->max_chunks + kDepWarps - 1) / kDepWarps;
+    const int blocks = (int)std::max(1LL, std::min(want, 8LL * sms));
+    k_cic_deposit_chunks<<<blocks, kDepWarps * 32, 0, st>>>(
+        pos, plan->ccs, (int)plan->total_cells, plan->chunk_cell, plan->slot_idx, 32 * plan->chunk_k, n_c, ratio,
+        wt, pm->box, pm->n / pm->box, mesh_exp(pm), pm->n, (float)scale, pm->fx);
+    SR_LAUNCH_CHECK("k_cic_deposit_chunks");
     pm->last_np = n;
     pm->deposited = true;
     pm->transformed = false;
