@@ -314,8 +314,9 @@ int sr_invariants_noalloc(int64_t n, const float* vel, const float* acc, double*
 /*
  * sr_plan_status -- synchronise the stream and report device-side flags of
  * the last calls: SR_ERR_CHECK if a bounds check of the checked build failed,
- * else SR_ERR_RANGE if sr_bin saw a non-finite or out-of-range position (the
- * reported flag is then cleared), else SR_OK.
+ * else SR_ERR_TIMEOUT if a bounded wait of sr_bin's radix sort ran out (its
+ * order is then not valid), else SR_ERR_RANGE if sr_bin saw a non-finite or
+ * out-of-range position (the reported flag is then cleared), else SR_OK.
  */
 int sr_plan_status(sr_plan* plan, void* stream);
 

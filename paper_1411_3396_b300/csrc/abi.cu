@@ -438,6 +438,11 @@ int sr_plan_status(sr_plan* p, void* stream) {
         return set_error(SR_ERR_CHECK, "bounds check " + std::to_string(chk) +
                                            " failed (bounds-checked build); the access was skipped");
     }
+    if (err & 2) {
+        SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->err, 0, sizeof(long long), st));
+        SR_CUDA_CHECK(cudaStreamSynchronize(st));
+        return set_error(SR_ERR_TIMEOUT, "a wait of the binning's radix sort ran out (the order is not valid)");
+    }
     if (err & 1) {
         SR_CUDA_CHECK(cudaMemsetAsync(&p->ctr->err, 0, sizeof(long long), st));
         SR_CUDA_CHECK(cudaStreamSynchronize(st));

@@ -298,7 +298,8 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, cons
         SR_LAUNCH_CHECK("k_keys");
     }
     int which = 0;
-    int rc = radix_sort_pairs(p->keys, p->vals, ni, p->key_bits, p->rs_particles, st, &which, &p->ctr->check);
+    int rc = radix_sort_pairs(p->keys, p->vals, ni, p->key_bits, p->rs_particles, st, &which, &p->ctr->check,
+                              &p->ctr->err);
     if (rc) return rc;
     p->sorted = which;
     const int tc = (int)p->total_cells;

@@ -563,7 +563,8 @@ int launch_cost_and_order(sr_plan* p, cudaStream_t st) {
     k_cost<<<(int)((mc + 255) / 256), 256, 0, st>>>(a, (int)mc, p->cost, p->lpt_keys[0], p->lpt_vals[0]);
     SR_LAUNCH_CHECK("k_cost");
     int which = 0;
-    int rc = radix_sort_pairs(p->lpt_keys, p->lpt_vals, (int)mc, 8, p->rs_chunks, st, &which, &p->ctr->check);
+    int rc = radix_sort_pairs(p->lpt_keys, p->lpt_vals, (int)mc, 8, p->rs_chunks, st, &which, &p->ctr->check,
+                              &p->ctr->err);
     if (rc) return rc;
     p->order = p->lpt_vals[which];
     return SR_OK;

@@ -2,15 +2,20 @@
 // passes) used by the binning step (Sec. 2.1 step 1: partition) and by the
 // longest-first work ordering.
 //
-// Radix pass = histogram per 2048-key tile -> exclusive scan of the
-// digit-major histogram -> stable scatter (the tile is first placed in
-// digit order in shared memory, so that the global writes of each digit's
-// run are contiguous).  Stability inside a tile: warp w
-// owns keys [256w, 256w+256) and walks them in rounds of 32; lanes holding
-// the same digit find each other with __match_any_sync, rank by lane order,
-// and a warp-private digit histogram in shared memory carries counts across
-// rounds; a per-digit prefix over the 8 warps orders warps.  The resulting
-// order is a pure function of the input: the sort is deterministic.
+// The sort is single-sweep: one kernel counts every pass's digits over the
+// whole key array at once (a digit's total does not depend on the order
+// the earlier passes leave), then each pass is one kernel.  A pass ranks a
+// 2048-key tile's digits (stable: warp w owns keys [256w, 256w+256) and
+// walks them in rounds of 32; lanes holding the same digit find each other
+// with __match_any_sync and rank by lane order; a warp-private digit
+// histogram in shared memory carries counts across rounds; a per-digit
+// prefix over the 8 warps orders warps), finds each digit's offset of the
+// tile by a decoupled look-back over the tiles before it, places the tile
+// in digit order in shared memory and writes each digit's run to
+// consecutive addresses.  Tiles take ids in the order their blocks start
+// (an atomic counter), so a tile waits only on tiles whose blocks are
+// already running; every wait is bounded.  The resulting order is a pure
+// function of the input: the sort is deterministic.
 #include "sr_internal.h"
 
 namespace sr {
@@ -78,36 +83,61 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int* out, int n, cons
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_radix_hist(const unsigned long long* __restrict__ keys,
-                                                              int n, int shift, int* hist, int n_tiles) {
-    __shared__ int h[kRadixBuckets];
-    for (int i = threadIdx.x; i < kRadixBuckets; i += blockDim.x) h[i] = 0;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * kScanTile;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const long long idx = base + k * kScanThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (kRadixBuckets - 1)], 1);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBuckets; d += blockDim.x) hist[(long long)d * n_tiles + blockIdx.x] = h[d];
+constexpr int kMaxPasses = 8;                          // 64-bit keys
+constexpr unsigned long long kLbAggregate = 1ull << 62;  // look-back word: tile count of a digit
+constexpr unsigned long long kLbPrefix = 2ull << 62;     // look-back word: inclusive prefix
+constexpr int kLbMaxSpins = 1 << 20;                    // bound of one look-back wait
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
+// Every pass's digit totals at once: totals[p * 256 + d].
+__global__ void __launch_bounds__(kScanThreads) k_radix_upsweep(const unsigned long long* __restrict__ keys,
+                                                                int n, int passes, int* __restrict__ totals) {
+    __shared__ int h[kMaxPasses][kRadixBuckets];
+    for (int i = threadIdx.x; i < kMaxPasses * kRadixBuckets; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[idx];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & (kRadixBuckets - 1)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadixBuckets; i += blockDim.x) {
+        const int v = (&h[0][0])[i];
+        if (v) atomicAdd(&totals[i], v);
+    }
+}
+
+// One pass (digit at bit `shift`, pass tag 1..8 in bits 56-61 of the
+// look-back words, which start cleared).  digit_total: this pass's 256
+// totals; status: 256 look-back words per tile; tile_counter: this pass's
+// tile-id counter.  A look-back wait that runs out sets bit 1 of *err.
+__global__ void __launch_bounds__(kScanThreads) k_radix_onesweep(
     const unsigned long long* __restrict__ kin, const int* __restrict__ vin,
-    unsigned long long* __restrict__ kout, int* __restrict__ vout, int n, int shift,
-    const int* __restrict__ hist_scan, int n_tiles, unsigned long long* check) {
+    unsigned long long* __restrict__ kout, int* __restrict__ vout, int n, int shift, int pass_tag,
+    const int* __restrict__ digit_total, unsigned long long* status, unsigned* tile_counter, long long* err,
+    unsigned long long* check) {
     constexpr int kWarps = kScanThreads / 32;
     __shared__ int wh[kWarps][kRadixBuckets];
     __shared__ int gbase[kRadixBuckets];
     __shared__ int loff[kRadixBuckets];
     __shared__ int wsum[kWarps];
+    __shared__ int s_tile;
     __shared__ unsigned long long skey[kScanTile];
     __shared__ int sval[kScanTile];
     for (int i = threadIdx.x; i < kWarps * kRadixBuckets; i += blockDim.x) (&wh[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
     __syncthreads();
+    const int tile = s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long base = (long long)blockIdx.x * kScanTile + warp * (kScanItems * 32);
+    const long long base = (long long)tile * kScanTile + warp * (kScanItems * 32);
     unsigned long long key[kScanItems];
     int val[kScanItems], dig[kScanItems], rnk[kScanItems];
     const unsigned lt = lanemask_lt();
@@ -126,8 +156,8 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
         rnk[r] = old + __popc(peers & lt);
     }
     __syncthreads();
-    // one digit per thread: prefix over the warps, the tile's count of the
-    // digit, and (block scan) the digit's first position inside the tile
+    // one digit per thread: prefix over the warps and the tile's count of
+    // the digit
     static_assert(kRadixBuckets == kScanThreads, "one digit per thread");
     const int d = threadIdx.x;
     int run = 0;
@@ -137,7 +167,46 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
         wh[w][d] = run;
         run += t;
     }
-    gbase[d] = hist_scan[(long long)d * n_tiles + blockIdx.x];
+    // the digit's offset of this tile: publish the tile's count, then add
+    // the predecessors' words back to one that holds an inclusive prefix
+    const unsigned long long tag = (unsigned long long)pass_tag << 56;
+    unsigned long long* mine = status + (long long)tile * kRadixBuckets + d;
+    long long excl = 0;
+    if (tile == 0) {
+        st_relaxed(mine, kLbPrefix | tag | (unsigned)run);
+    } else {
+        st_relaxed(mine, kLbAggregate | tag | (unsigned)run);
+        int j = tile - 1, spins = 0;
+        while (j >= 0) {
+            const unsigned long long v = ld_relaxed(status + (long long)j * kRadixBuckets + d);
+            if ((int)((v >> 56) & 63) != pass_tag) {                  // not published yet
+                if (++spins > kLbMaxSpins) {
+                    if (err) atomicOr((unsigned long long*)err, 2ull);
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            excl += (unsigned)v;
+            if ((v >> 62) == 2ull) break;                              // inclusive prefix reached
+            --j;
+        }
+        st_relaxed(mine, kLbPrefix | tag | (unsigned)(excl + run));
+    }
+    // digit bases: exclusive scan of the pass's totals
+    const int tot = digit_total[d];
+    const int incl_t = warp_inclusive_scan(tot);
+    if (lane == 31) wsum[warp] = incl_t;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < kWarps ? wsum[lane] : 0;
+        v = warp_inclusive_scan(v);
+        if (lane < kWarps) wsum[lane] = v;
+    }
+    __syncthreads();
+    gbase[d] = (warp > 0 ? wsum[warp - 1] : 0) + incl_t - tot + (int)excl;
+    __syncthreads();
+    // the tile's digit offsets inside the tile
     const int incl = warp_inclusive_scan(run);
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
@@ -162,7 +231,7 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_scatter(
     __syncthreads();
     // ... then written out by consecutive threads to consecutive addresses
     // of each digit's run
-    const long long tile0 = (long long)blockIdx.x * kScanTile;
+    const long long tile0 = (long long)tile * kScanTile;
     const int cnt = (int)(n - tile0 < kScanTile ? n - tile0 : kScanTile);
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         const unsigned long long k = skey[t];
@@ -222,38 +291,46 @@ int exclusive_scan(const int* in, int* out, int n, ScanScratch& s, cudaStream_t 
 int radix_alloc(RadixScratch& r, long long n) {
     radix_free(r);
     r.max_tiles = tiles_of(n > 0 ? n : 1);
-    const size_t hn = (size_t)kRadixBuckets * r.max_tiles;
-    cudaError_t e = cudaMalloc(&r.hist, sizeof(int) * hn);
+    r.bytes = sizeof(int) * (kMaxPasses * kRadixBuckets + kMaxPasses) +
+              sizeof(unsigned long long) * (size_t)kRadixBuckets * r.max_tiles;
+    cudaError_t e = cudaMalloc(&r.region, r.bytes);
     if (e != cudaSuccess) return cuda_fail(e, "radix_alloc");
-    e = cudaMalloc(&r.hist_scan, sizeof(int) * hn);
-    if (e != cudaSuccess) return cuda_fail(e, "radix_alloc");
-    return scan_alloc(r.scan, (long long)hn);
+    return SR_OK;
 }
 
 void radix_free(RadixScratch& r) {
-    if (r.hist) cudaFree(r.hist);
-    if (r.hist_scan) cudaFree(r.hist_scan);
-    r.hist = r.hist_scan = nullptr;
+    if (r.region) cudaFree(r.region);
+    r.region = nullptr;
+    r.bytes = 0;
     r.max_tiles = 0;
-    scan_free(r.scan);
 }
 
 int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_bits,
-                     RadixScratch& r, cudaStream_t st, int* which, unsigned long long* check) {
+                     RadixScratch& r, cudaStream_t st, int* which, unsigned long long* check, long long* err) {
     int cur = 0;
     *which = 0;
     if (n <= 0) return SR_OK;
     const int t = tiles_of(n);
     if (t > r.max_tiles) return set_error(SR_ERR_CAPACITY, "radix scratch too small");
-    const int hn = kRadixBuckets * t;
-    for (int shift = 0; shift < key_bits; shift += kRadixBits) {
-        k_radix_hist<<<t, kScanThreads, 0, st>>>(keys[cur], n, shift, r.hist, t);
-        SR_LAUNCH_CHECK("k_radix_hist");
-        int rc = exclusive_scan(r.hist, r.hist_scan, hn, r.scan, st);
-        if (rc) return rc;
-        k_radix_scatter<<<t, kScanThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n,
-                                                    shift, r.hist_scan, t, check);
-        SR_LAUNCH_CHECK("k_radix_scatter");
+    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    if (passes > kMaxPasses) return set_error(SR_ERR_ARG, "radix keys wider than 64 bits");
+    if (passes == 0) return SR_OK;
+    // region: totals (passes x 256), tile counters (passes), look-back words (256 per tile)
+    int* totals = static_cast<int*>(r.region);
+    unsigned* counters = reinterpret_cast<unsigned*>(totals + kMaxPasses * kRadixBuckets);
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(
+        static_cast<char*>(r.region) + sizeof(int) * (kMaxPasses * kRadixBuckets + kMaxPasses));
+    const size_t used = sizeof(int) * (kMaxPasses * kRadixBuckets + kMaxPasses) +
+                        sizeof(unsigned long long) * (size_t)kRadixBuckets * t;
+    SR_CUDA_CHECK(cudaMemsetAsync(r.region, 0, used, st));
+    const int ub = t < 1024 ? t : 1024;
+    k_radix_upsweep<<<ub, kScanThreads, 0, st>>>(keys[0], n, passes, totals);
+    SR_LAUNCH_CHECK("k_radix_upsweep");
+    for (int p = 0; p < passes; ++p) {
+        k_radix_onesweep<<<t, kScanThreads, 0, st>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], n,
+                                                     kRadixBits * p, p + 1, totals + kRadixBuckets * p, status,
+                                                     counters + p, err, check);
+        SR_LAUNCH_CHECK("k_radix_onesweep");
         cur = 1 - cur;
     }
     *which = cur;

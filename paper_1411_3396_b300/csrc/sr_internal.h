@@ -180,10 +180,9 @@ struct ScanScratch {
 };
 
 struct RadixScratch {
-    int* hist = nullptr;          // kRadixBuckets * n_tiles
-    int* hist_scan = nullptr;
+    void* region = nullptr;       // digit totals, tile counters, look-back words (radix.cu)
+    size_t bytes = 0;
     int max_tiles = 0;
-    ScanScratch scan;
 };
 
 }  // namespace sr
@@ -281,8 +280,10 @@ int radix_alloc(RadixScratch& r, long long n);
 void radix_free(RadixScratch& r);
 // Sorts (keys[0], vals[0]) stably by the low key_bits bits; returns in *which
 // the index (0/1) of the buffer pair that holds the result.
+// A look-back wait that runs out sets bit 1 of *err (nullable).
 int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_bits,
-                     RadixScratch& r, cudaStream_t st, int* which, unsigned long long* check = nullptr);
+                     RadixScratch& r, cudaStream_t st, int* which, unsigned long long* check = nullptr,
+                     long long* err = nullptr);
 
 // binning (bin.cu)
 int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st,
