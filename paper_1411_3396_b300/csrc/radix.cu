@@ -87,6 +87,7 @@ constexpr int kMaxPasses = 8;                          // 64-bit keys
 constexpr unsigned long long kLbAggregate = 1ull << 62;  // look-back word: tile count of a digit
 constexpr unsigned long long kLbPrefix = 2ull << 62;     // look-back word: inclusive prefix
 constexpr int kLbMaxSpins = 1 << 20;                    // bound of one look-back wait
+constexpr int kLbWindow = 8;                            // look-back words loaded at once
 
 __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -176,20 +177,34 @@ __global__ void __launch_bounds__(kScanThreads) k_radix_onesweep(
         st_relaxed(mine, kLbPrefix | tag | (unsigned)run);
     } else {
         st_relaxed(mine, kLbAggregate | tag | (unsigned)run);
+        // predecessors in windows of kLbWindow words loaded together (the
+        // walk is a chain of dependent loads otherwise)
         int j = tile - 1, spins = 0;
-        while (j >= 0) {
-            const unsigned long long v = ld_relaxed(status + (long long)j * kRadixBuckets + d);
-            if ((int)((v >> 56) & 63) != pass_tag) {                  // not published yet
+        bool done = false;
+        while (j >= 0 && !done) {
+            unsigned long long w[kLbWindow];
+            const int m = j + 1 < kLbWindow ? j + 1 : kLbWindow;
+#pragma unroll
+            for (int q = 0; q < kLbWindow; ++q)
+                w[q] = q < m ? ld_relaxed(status + (long long)(j - q) * kRadixBuckets + d) : 0ull;
+            int q = 0;
+            for (; q < m; ++q) {
+                if ((int)((w[q] >> 56) & 63) != pass_tag) break;        // not published yet
+                excl += (unsigned)w[q];
+                if ((w[q] >> 62) == 2ull) {                             // inclusive prefix reached
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            j -= q;
+            if (q < m) {                                                // wait for tile j
                 if (++spins > kLbMaxSpins) {
                     if (err) atomicOr((unsigned long long*)err, 2ull);
                     break;
                 }
-                __nanosleep(64);
-                continue;
+                __nanosleep(32);
             }
-            excl += (unsigned)v;
-            if ((v >> 62) == 2ull) break;                              // inclusive prefix reached
-            --j;
         }
         st_relaxed(mine, kLbPrefix | tag | (unsigned)(excl + run));
     }
