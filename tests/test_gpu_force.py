@@ -265,3 +265,44 @@ def test_newton_third_law_on_gpu():
     vel = torch.zeros((acc.shape[0], 4), dtype=torch.float32, device="cuda")
     inv = to_np(plan.invariants(vel, torch.from_numpy(acc).cuda()))
     assert np.all(np.abs(inv[3:6]) <= 1e-5 * np.abs(acc[:, :3]).sum())
+
+
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_passive_particles_every_variant(chunk):
+    # sr_bin_active: with every other particle passive, each variant writes
+    # the active rows with the unmasked run's bits (chunks holding an active
+    # particle run unchanged), leaves passive rows untouched, and counts the
+    # active rows' pairs; with no active particle nothing is written
+    from paper_1411_3396_b300 import SrError
+    w = _work("clustered256")
+    (pos, box), = w["volumes"]
+    x = torch.from_numpy(pos).cuda()
+    n = len(pos)
+    plan = make_plan(w["volumes"], w["params"], chunk_size=chunk)
+    active = torch.zeros(n, dtype=torch.bool, device="cuda")
+    active[::2] = True
+    act = to_np(active)
+    for v in range(17):
+        plan.bin(x)
+        try:
+            plan.set_variant(v)
+        except SrError:
+            continue
+        full, pairs_full, pp_full = plan.force(count=True, per_particle=True)
+        full, pp_full = to_np(full), to_np(pp_full)
+        ref = to_np(plan.force())
+        plan.bin(x, active=active)
+        acc = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+        got = to_np(plan.force(acc))
+        assert got[act].tobytes() == ref[act].tobytes(), f"variant {v}"
+        assert np.all(np.isnan(got[~act])), f"variant {v}"
+        pp = torch.full((n,), -5, dtype=torch.int32, device="cuda")
+        _, pairs, pp = plan.force(count=True, per_particle=pp)
+        pp = to_np(pp)
+        assert np.array_equal(pp[act], pp_full[act]) and np.all(pp[~act] == -5), f"variant {v}"
+        assert int(pairs.item()) == int(pp_full[act].sum()), f"variant {v}"
+    plan.bin(x, active=torch.zeros(n, dtype=torch.bool, device="cuda"))
+    acc = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+    assert np.all(np.isnan(to_np(plan.force(acc))))
+    assert plan.export("counters").cpu().numpy()[5] == 0          # no work items
+    plan.status()
