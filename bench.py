@@ -1510,6 +1510,7 @@ def run_diff(args, rank, world, local_rank):
                    "trajectories_per_s": 1e3 / ms, "loss": float(loss.item()),
                    "graph": not args.no_graph, "eager_ms_per_step": eager_ms,
                    "plans": 1 if isinstance(traj_plans, Plan) else len(traj_plans),
+                   "variant": plan.info()["variant"],
                    "binnings_per_trajectory": steps if not isinstance(traj_plans, Plan) else 2 * steps,
                    "parallelism": "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

@@ -525,20 +525,31 @@ void launch_mode(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
 
 // The VJP kernel: packed f32x2 pair loop for 32-particle chunks, the scalar
 // loop for 64-particle chunks.
-// The VJP follows the neighbour enumeration of the selected force variant:
-// the flat one when the autotuner (or the caller) chose a flat or grouped
-// variant, i.e. at low density; the same chunks in the same order either
-// way, so the results are the same bits.
+// The VJP follows the selected force variant (the autotuner's reading of
+// the density): the flat neighbour enumeration with variants 13-16, and
+// packed batches of 64 staged neighbours with variants 12, 14-16 (else
+// 128).  The enumeration does not change the bits; the batch size groups
+// the compensated sums differently.
+template <int K, int FLAGS>
+void launch_vjp_f(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
+    const VolDev& v0 = p->vols_h[0];
+    if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, FLAGS, true><<<blocks, kThreads, 0, st>>>(a, v0);
+    else k_pairs<kVjp, K, 8, kVjpMinBlocks, FLAGS, false><<<blocks, kThreads, 0, st>>>(a, v0);
+}
+
 template <int K>
 void launch_vjp(sr_plan* p, const Args& a, int blocks, cudaStream_t st) {
-    const VolDev& v0 = p->vols_h[0];
-    const bool flat = K == 1 && p->variant >= 13;
-    if (flat) {
-        if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K) | kVjpFlat, true><<<blocks, kThreads, 0, st>>>(a, v0);
-        else k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K) | kVjpFlat, false><<<blocks, kThreads, 0, st>>>(a, v0);
+    if constexpr (K == 1) {
+        const int v = p->variant;
+        const bool flat = v >= 13;
+        const bool b64 = v == 12 || v >= 14;
+        constexpr int F = vjp_flags(K);
+        if (flat && b64) launch_vjp_f<K, F | kVjpFlat | 4>(p, a, blocks, st);
+        else if (flat) launch_vjp_f<K, F | kVjpFlat>(p, a, blocks, st);
+        else if (b64) launch_vjp_f<K, F | 4>(p, a, blocks, st);
+        else launch_vjp_f<K, F>(p, a, blocks, st);
     } else {
-        if (p->n_vol == 1) k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), true><<<blocks, kThreads, 0, st>>>(a, v0);
-        else k_pairs<kVjp, K, 8, kVjpMinBlocks, vjp_flags(K), false><<<blocks, kThreads, 0, st>>>(a, v0);
+        launch_vjp_f<K, vjp_flags(K)>(p, a, blocks, st);
     }
 }
 

@@ -58,20 +58,30 @@ def test_vjp_on_a_batch_plan(chunk):
 
 
 @pytest.mark.parametrize("name", ["diff64", "clustered256"])
-def test_vjp_flat_enumeration_same_bits(name):
-    # the VJP follows the selected force variant's neighbour enumeration,
-    # flat (variants 13-16) or cell by cell: the same chunks in the same
-    # order, so the same bits
-    w = wc.make_workload(wc.small_variant(name))
-    (pos, box), = w["volumes"]
-    plan = make_plan(w["volumes"], w["params"])
+def test_vjp_follows_the_force_variant(name):
+    # the VJP follows the selected force variant: the flat neighbour
+    # enumeration with 13-16 (the same chunks in the same order, so the same
+    # bits as cell by cell) and packed batches of 64 with 12 and 14-16
+    # (else 128); both batch sizes meet the oracle bar
+    prm_w = wc.make_workload(wc.small_variant(name))
+    (pos, box), = prm_w["volumes"]
+    prm = prm_w["params"]
+    plan = make_plan(prm_w["volumes"], prm)
     plan.bin(torch.from_numpy(pos).cuda())
     g = torch.from_numpy(_g(len(pos), 5)).cuda()
     plan.set_variant(11)
-    a = to_np(plan.vjp(g))
-    for v in (14, 15):
+    a128 = to_np(plan.vjp(g))
+    plan.set_variant(13)
+    assert to_np(plan.vjp(g)).tobytes() == a128.tobytes(), "variant 13"
+    plan.set_variant(12)
+    a64 = to_np(plan.vjp(g))
+    for v in (14, 15, 16):
         plan.set_variant(v)
-        assert to_np(plan.vjp(g)).tobytes() == a.tobytes(), f"variant {v}"
+        assert to_np(plan.vjp(g)).tobytes() == a64.tobytes(), f"variant {v}"
+    c = ofit.fit_poly(prm["rc"], prm["sigma"], prm["eps"])
+    ref = oint.force_vjp(pos, box, prm["rc"], prm["eps"], c, g.cpu().numpy()[:, :3].astype(np.float64))
+    assert_force_close(a128, ref, f"vjp {name} batches of 128")
+    assert_force_close(a64, ref, f"vjp {name} batches of 64")
 
 
 def test_vjp_scale_and_accumulate():
