@@ -78,12 +78,29 @@ __global__ void __launch_bounds__(256) k_inv_partial(long long n, const float4* 
     if (threadIdx.x < 7) partials[(long long)blockIdx.x * 7 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void k_inv_final(const double* __restrict__ partials, int blocks, double* __restrict__ out) {
-    if (threadIdx.x < 7) {
-        double s = 0.0;
-        for (int b = 0; b < blocks; ++b) s += partials[(long long)b * 7 + threadIdx.x];
-        out[threadIdx.x] = s;
+// The blocks' partial sums added by one block: each thread sums a fixed
+// strided subset, then a fixed tree; deterministic (a single thread walking
+// all partials in order was latency-bound: some 1,200 dependent binary64
+// adds per sum).
+__global__ void __launch_bounds__(256) k_inv_final(const double* __restrict__ partials, int blocks,
+                                                   double* __restrict__ out) {
+    __shared__ double sh[7][256];
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s[k] += partials[(long long)b * 7 + k];
     }
+#pragma unroll
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 int grid_for(long long n) {
@@ -121,7 +138,7 @@ int launch_invariants(long long n, const float* vel, const float* acc, double* o
     k_inv_partial<<<kInvBlocks, 256, 0, st>>>(n, reinterpret_cast<const float4*>(vel),
                                               reinterpret_cast<const float4*>(acc), partials);
     SR_LAUNCH_CHECK("k_inv_partial");
-    k_inv_final<<<1, 32, 0, st>>>(partials, kInvBlocks, out);
+    k_inv_final<<<1, 256, 0, st>>>(partials, kInvBlocks, out);
     SR_LAUNCH_CHECK("k_inv_final");
     return SR_OK;
 }
