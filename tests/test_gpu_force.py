@@ -153,9 +153,10 @@ def test_grouped_variants_forces_and_counts(small_case):
         assert again.tobytes() == acc.tobytes(), f"variant {v} not deterministic"
 
 
-def test_grouped_variants_brute_force_tiny_boxes():
-    # boxes of 2 to 4 cells per axis: chunks see their own images through
-    # several faces, ragged groups in nearly every chunk
+def test_flat_and_grouped_variants_brute_force_tiny_boxes():
+    # boxes of 1 to 2 cells per axis: the flat enumeration's 27 neighbour
+    # lanes map to a few cells under several image shifts, chunks see their
+    # own images through several faces, ragged groups in nearly every chunk
     for L, n, seed in [(7.0, 300, 1), (8.0, 512, 2), (10.0, 400, 3), (6.5, 64, 4), (9.0, 37, 5)]:
         pos = gen.uniform_box(n, L, seed)
         params = dict(rc=3.0, eps=0.1, sigma=0.8)
@@ -163,7 +164,7 @@ def test_grouped_variants_brute_force_tiny_boxes():
         a_ref, cnt = oforce.accel_brute(pos, L, 3.0, 0.1, c)
         plan = make_plan([(pos, L)], params)
         plan.bin(torch.from_numpy(pos).cuda())
-        for v in GROUPED:
+        for v in (13, 14, *GROUPED):
             plan.set_variant(v)
             acc, pairs, pp = plan.force(count=True, per_particle=True)
             assert_force_close(to_np(acc), a_ref, f"L={L} variant {v}")
