@@ -134,20 +134,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_grp(const Args a, co
             const ulonglong2* A2 = reinterpret_cast<const ulonglong2*>(A);
             const f2* B2 = reinterpret_cast<const f2*>(B);
             const int m0 = (rd >> 1) + jp;
-            if (padded == kBatch) {
-#pragma unroll
-                for (int t = 0; t < kBatch / (2 * J); ++t) {
-                    const int m = (m0 + J * t) & (RING / 2 - 1);
-                    const ulonglong2 e = A2[m];
-                    pair_force2<CNT>(e.x, e.y, B2[m], XI, YI, ZI, PK, PX, PY, PZ, np);
-                }
-            } else {
-                const int iters = padded / (2 * J);
-                for (int t = 0; t < iters; ++t) {
-                    const int m = (m0 + J * t) & (RING / 2 - 1);
-                    const ulonglong2 e = A2[m];
-                    pair_force2<CNT>(e.x, e.y, B2[m], XI, YI, ZI, PK, PX, PY, PZ, np);
-                }
+            // one loop for full and partial batches (a small instruction
+            // footprint: the batch is inlined at three call sites)
+            const int iters = padded / (2 * J);
+#pragma unroll 4
+            for (int t = 0; t < iters; ++t) {
+                const int m = (m0 + J * t) & (RING / 2 - 1);
+                const ulonglong2 e = A2[m];
+                pair_force2<CNT>(e.x, e.y, B2[m], XI, YI, ZI, PK, PX, PY, PZ, np);
             }
             float e0, o0;
             f2_unpack(PX, e0, o0); float px = e0 + o0;
