@@ -170,8 +170,8 @@ def time_hbm_kernels(plan, x, acc, vel, n, hbm_gbs, reps=5):
                           ("sr_kick", ev[2].elapsed_time(ev[3]) / reps, KICK_BYTES_PER_PARTICLE)):
         gbs = n * bpp / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "bytes_per_particle": bpp, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm_gbs}
-    out["note"] = ("sr_bin includes the 5-pass radix sort and the gather of positions into slots; "
-                   "the time step fuses the kick into the force kernel")
+    out["note"] = ("sr_bin includes the counting sort by cell, the per-cell sorts and the gather of "
+                   "positions into slots; the time step fuses the kick into the force kernel")
     return out
 
 

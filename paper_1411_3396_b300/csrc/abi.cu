@@ -41,7 +41,6 @@ void free_plan(sr_plan* p) {
         cudaFree(p->lpt_vals[k]);
     }
     cudaFree(p->cell_start);
-    cudaFree(p->cell_nch);
     cudaFree(p->ccs);
     cudaFree(p->chunk_cell);
     cudaFree(p->chunk_meta);
@@ -59,9 +58,8 @@ void free_plan(sr_plan* p) {
     if (p->h_side) cudaStreamDestroy(p->h_side);
     if (p->h_fork) cudaEventDestroy(p->h_fork);
     if (p->h_join) cudaEventDestroy(p->h_join);
-    radix_free(p->rs_particles);
     radix_free(p->rs_chunks);
-    scan_free(p->scan_cells);
+    bin_free(p);
     delete p;
 }
 
@@ -211,7 +209,6 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
         SR_ALLOC(p->lpt_vals[k], mc);
     }
     SR_ALLOC(p->cell_start, cells + 1);
-    SR_ALLOC(p->cell_nch, cells + 1);
     SR_ALLOC(p->ccs, cells + 1);
     SR_ALLOC(p->chunk_cell, mc);
     SR_ALLOC(p->chunk_meta, mc);
@@ -224,8 +221,7 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
     SR_ALLOC(p->ctr, 1);
     SR_ALLOC(p->inv_partials, (size_t)kInvBlocks * 7);
 #undef SR_ALLOC
-    if ((rc = radix_alloc(p->rs_particles, cap)) || (rc = radix_alloc(p->rs_chunks, mc)) ||
-        (rc = scan_alloc(p->scan_cells, cells + 1))) {
+    if ((rc = radix_alloc(p->rs_chunks, mc)) || (rc = bin_alloc(p))) {
         free_plan(p);
         return rc;
     }

@@ -8,9 +8,33 @@
 //   fold      x < 0 -> x + L, then x >= L -> x - L     (inputs in [-L, 2L))
 //   t = x / h (binary64, round to nearest), q = min(floor(t), M - 1)
 //   cell = q >> b, sub = q & (2^b - 1), global cell id volume-major,
-//   key = (cell << 3b) | morton(sub);  stable sort by key (LSD radix)
+//   key = (cell << 3b) | morton(sub); order by key, ties by caller index
 //   chunks = runs of <= 32 consecutive particles inside a cell
 //   anchor qA = q of the chunk's first particle, offset = binary32(t - qA)
+//
+// The order is reached by a counting sort on the cell, then a sort of each
+// cell on the composite (morton(sub) << ib) | caller index, ib = bits of a
+// caller index:
+//   k_keys           cell and Morton code per particle; per-cell counts
+//                    taken with atomics give each particle a place in its
+//                    cell (in no fixed order)
+//   k_cell_scan      one pass over the cells (decoupled look-back): cell
+//                    starts, chunk starts and the chunk -> cell map; cells
+//                    of 2..kWarpSeg particles are listed for a warp sort,
+//                    larger ones up to kSegTile for a block sort, the rest
+//                    as huge
+//   k_scatter        each particle's composite into its cell's range
+//   k_split          one block per huge cell splits it on the composite's
+//                    top 8 bits into up to 256 buckets, which are listed
+//   k_sort_segments  the listed ranges: a warp each (bitonic in registers
+//                    up to kSmallCell, else a stable LSD sort on 8-bit
+//                    digits in the warp's shared memory), then a block each
+//                    for the block list (the same LSD sort, through global
+//                    memory above kSegTile)
+//   k_chunk_fill     one warp per chunk: slots from the sorted composites
+// The composites of a cell are distinct (the caller index is part of
+// them), so each cell ends in the spec's order whatever order the atomics
+// left, and the result is a pure function of the input.
 #include "sr_internal.h"
 
 namespace sr {
@@ -94,6 +118,32 @@ __device__ __forceinline__ bool fine_axis_quot(double x, unsigned long long ubox
     return true;
 }
 
+// floor(x / h) alone (the cell and Morton code need nothing more), from
+// one product t' = x y, y = RN(1/h), instead of the corrected quotient:
+// t' carries two roundings of relative size 2^-53, so it lies within
+// 2.5 ulp of RN(x / h), and floor(t') = floor(RN(x / h)) whenever t' is
+// 16 ulps or more from every integer.  Returns false otherwise (and for
+// whatever fine_axis_quot declines), and the caller takes the corrected
+// quotient.
+__device__ __forceinline__ bool fine_axis_floor(double x, unsigned long long ubox, double y, int& q) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if (u >= ubox || u < (123ull << 52)) return false;       // outside [2^-900, box)
+    const unsigned long long ut = (unsigned long long)__double_as_longlong(x * y);
+    const int E = (int)(ut >> 52) - 1023;
+    if (E < 0) {                                              // t' < 1
+        if (ut >= 0x3FEFFFFFFFFFFFF0ull) return false;       // within 16 ulps of 1
+        q = 0;
+        return true;
+    }
+    if (E > 47) return false;
+    const int F = 52 - E;
+    const unsigned long long mant = (ut & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned long long frac = mant & ((1ull << F) - 1ull);
+    if (frac < 16ull || frac > (1ull << F) - 16ull) return false;
+    q = (int)(mant >> F);
+    return true;
+}
+
 // Fine-grid coordinate of one axis; flags non-finite / out-of-range input.
 __device__ __forceinline__ void fine_axis(double x, const VolDev& V, double& t, int& q, bool& bad) {
     const double box = V.box;
@@ -112,220 +162,831 @@ __device__ __forceinline__ void fine_axis(double x, const VolDev& V, double& t, 
     q = qq;
 }
 
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr int kSmallCell = 128;                 // ranges sorted by one warp in registers (bitonic)
+constexpr int kWarpSeg = 512;                   // ranges sorted by one warp in shared memory (LSD)
+constexpr int kWarpRounds = kWarpSeg / 32;
+constexpr int kSegTile = 2048;                  // elements a block-sort holds in shared memory
+constexpr int kSegThreads = 256;                // one 8-bit digit per thread
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegRounds = kSegTile / kSegThreads;
+constexpr int kSegMaxPasses = 8;                // composites of up to 64 bits
+// k_sort_segments' dynamic shared memory: two kWarpSeg halves per warp in
+// the warp phase; kSegTile values and the pass histograms in the block phase
+constexpr int kSortSmem = (int)sizeof(unsigned long long) * 2 * kSegWarps * kWarpSeg;
+static_assert(sizeof(unsigned long long) * kSegTile + sizeof(int) * kSegMaxPasses * 256 <= (size_t)kSortSmem,
+              "block phase fits in the warp phase's shared memory");
+constexpr int kSplitThreads = 512;
+constexpr int kCellTile = kScanTile;            // cells per block of the cell scan
+constexpr unsigned long long kLbAggregate = 1ull << 62;   // look-back word: the tile's own sums
+constexpr unsigned long long kLbPrefix = 2ull << 62;      // look-back word: inclusive prefix
+constexpr int kLbMaxSpins = 1 << 20;            // bound of one look-back wait
+
+__device__ __forceinline__ int block_exclusive_scan256(int v, int* warp_tot) {
+    // 256 threads, one value each; warp_tot: 8 ints of shared memory
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) before += w < warp ? warp_tot[w] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+// Bitonic sort of 32 S values held as v[s] at lane l (element l + 32 s),
+// ascending.
+template <int S>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[S]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32 * S; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int js = j >> 5;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    if (s & js) continue;
+                    const bool asc = ((lane + 32 * s) & k) == 0;
+                    const unsigned long long x = v[s], y = v[s | js];
+                    if ((x > y) == asc) {
+                        v[s] = y;
+                        v[s | js] = x;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    const unsigned long long y = __shfl_xor_sync(kFull, v[s], j);
+                    const bool asc = ((lane + 32 * s) & k) == 0, lower = (lane & j) == 0;
+                    const unsigned long long lo = v[s] < y ? v[s] : y, hi = v[s] < y ? y : v[s];
+                    v[s] = lower == asc ? lo : hi;
+                }
+            }
+        }
+    }
+}
+
+// One warp sorts src[0, m) (m <= 32 S) into dst[0, m) (dst may be src).
+template <int S>
+__device__ __forceinline__ void warp_sort_copy(const unsigned long long* src, unsigned long long* dst, int m) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long v[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) v[s] = lane + 32 * s < m ? src[lane + 32 * s] : ~0ull;
+    warp_bitonic<S>(v);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+        if (lane + 32 * s < m) dst[lane + 32 * s] = v[s];
+}
+
+__device__ __forceinline__ void warp_sort_small(const unsigned long long* src, unsigned long long* dst, int m) {
+    if (m <= 32) warp_sort_copy<1>(src, dst, m);
+    else if (m <= 64) warp_sort_copy<2>(src, dst, m);
+    else warp_sort_copy<4>(src, dst, m);
+}
+
+// Shared-memory counters ctr[key] += 1 for every lane with ok, one atomic
+// per distinct key of the warp; returns the counter's value before this
+// lane's unit (lanes of one key in lane order).
+__device__ __forceinline__ int warp_add(int* ctr, int key, bool ok) {
+    const unsigned peers = __match_any_sync(kFull, ok ? key : -1);
+    const int leader = __ffs(peers) - 1;
+    int old = 0;
+    if (ok && (threadIdx.x & 31) == leader) old = atomicAdd(ctr + key, __popc(peers));
+    old = __shfl_sync(kFull, old, leader);
+    return old + __popc(peers & lanemask_lt());
+}
+
+// One warp sorts src[0, m) (m <= kWarpSeg) by the low `bits` bits into
+// dst[0, m): a stable LSD sort on 8-bit digits through buf (2 kWarpSeg
+// values) with 256 counters in cnt, all the warp's own shared memory.  A
+// pass ranks each value among the earlier ones of its digit (32 at a
+// time, lanes of one digit in lane order), scans the counts and scatters
+// into the other half of buf; passes whose digit is the same throughout
+// are skipped.
+__device__ void warp_lsd(const unsigned long long* src, unsigned long long* dst, int m, int bits,
+                         unsigned long long* buf, int* cnt) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    unsigned long long* cur = buf;
+    unsigned long long* nxt = buf + kWarpSeg;
+    for (int e = lane; e < m; e += 32) cur[e] = src[e];
+    __syncwarp();
+    const int rounds = (m + 31) >> 5;
+    const int passes = (bits + 7) >> 3;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        for (int d = lane; d < 256; d += 32) cnt[d] = 0;
+        __syncwarp();
+        int rk[kWarpRounds];
+#pragma unroll
+        for (int r = 0; r < kWarpRounds; ++r) {
+            rk[r] = 0;
+            if (r < rounds) {
+                const int e = r * 32 + lane;
+                const bool ok = e < m;
+                const int d = ok ? (int)((cur[e] >> shift) & 255ull) : 256;
+                const unsigned peers = __match_any_sync(kFull, d);
+                const int old = ok ? cnt[d] : 0;
+                __syncwarp();
+                if (ok && lane == __ffs(peers) - 1) cnt[d] = old + __popc(peers);
+                __syncwarp();
+                rk[r] = old + __popc(peers & lt);
+            }
+        }
+        int loc[8], sum = 0;
+        bool whole = false;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            loc[t] = cnt[8 * lane + t];
+            sum += loc[t];
+            whole = whole || loc[t] == m;
+        }
+        if (__any_sync(kFull, whole)) continue;          // one digit throughout: order kept
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += t;
+        }
+        int run = x - sum;
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            cnt[8 * lane + t] = run;
+            run += loc[t];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kWarpRounds; ++r) {
+            const int e = r * 32 + lane;
+            if (r < rounds && e < m) {
+                const unsigned long long v = cur[e];
+                nxt[cnt[(int)((v >> shift) & 255ull)] + rk[r]] = v;
+            }
+        }
+        __syncwarp();
+        unsigned long long* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int e = lane; e < m; e += 32) dst[e] = cur[e];
+}
+
+// Cell and Morton code of every particle, and its place in its cell from
+// the cell's count (warp-aggregated atomics: lanes of one cell take one
+// atomic).
 __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, int n,
                                               const VolDev* __restrict__ vols,
                                               const long long* __restrict__ part_start, int n_vol,
                                               int b, unsigned long long* __restrict__ keys,
-                                              int* __restrict__ vals, Counters* ctr) {
+                                              int* __restrict__ place, int* __restrict__ count,
+                                              Counters* ctr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int v = n_vol > 1 ? volume_of_row(i, part_start, n_vol) : 0;
-    const VolDev& V = vols[v];
+    const int lane = threadIdx.x & 31;
+    bool ok = i < n;
+    int cell = 0;
+    unsigned long long m = 0ull;
     bool bad = false;
-    int q[3];
-    const double x3[3] = {pos[3ll * i], pos[3ll * i + 1], pos[3ll * i + 2]};
-    bool fast = true;
-    {
-        const unsigned long long ubox = (unsigned long long)__double_as_longlong(V.box);
-        unsigned long long mant;
-        int F;
-        if (V.h_pow2) {
+    if (ok) {
+        const int v = n_vol > 1 ? volume_of_row(i, part_start, n_vol) : 0;
+        const VolDev& V = vols[v];
+        int q[3];
+        const double x3[3] = {pos[3ll * i], pos[3ll * i + 1], pos[3ll * i + 2]};
+        bool fast = true;
+        {
+            const unsigned long long ubox = (unsigned long long)__double_as_longlong(V.box);
+            unsigned long long mant;
+            int F;
+            if (V.h_pow2) {
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) fast = fast && fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[ax], mant, F);
-        } else {
+                for (int ax = 0; ax < 3; ++ax) fast = fast && fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[ax], mant, F);
+            } else {
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                fast = fast && fine_axis_quot(x3[ax], ubox, V.h, V.inv_h, q[ax], mant, F);
-                q[ax] = min(q[ax], V.M - 1);
+                for (int ax = 0; ax < 3; ++ax) {
+                    fast = fast && fine_axis_floor(x3[ax], ubox, V.inv_h, q[ax]);
+                    q[ax] = min(q[ax], V.M - 1);
+                }
             }
         }
-    }
-    if (!fast) {
-        double t[3];
+        if (!fast) {
+            double t[3];
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) fine_axis(x3[ax], V, t[ax], q[ax], bad);
+            for (int ax = 0; ax < 3; ++ax) fine_axis(x3[ax], V, t[ax], q[ax], bad);
+        }
+        const int mask = (1 << b) - 1;
+        cell = V.cell_base + ((q[2] >> b) * V.n_c + (q[1] >> b)) * V.n_c + (q[0] >> b);
+        m = spread3(q[0] & mask) | (spread3(q[1] & mask) << 1) | (spread3(q[2] & mask) << 2);
+        ok = SR_BOUND(cell >= V.cell_base && cell < V.cell_base + V.n_c * V.n_c * V.n_c, &ctr->check,
+                      kChkKeyCell);
     }
-    const int mask = (1 << b) - 1;
-    const int cell = V.cell_base + ((q[2] >> b) * V.n_c + (q[1] >> b)) * V.n_c + (q[0] >> b);
-    const unsigned long long m = spread3(q[0] & mask) | (spread3(q[1] & mask) << 1) |
-                                 (spread3(q[2] & mask) << 2);
-    if (!SR_BOUND(cell >= V.cell_base && cell < V.cell_base + V.n_c * V.n_c * V.n_c, &ctr->check, kChkKeyCell))
-        return;
+    const unsigned live = __ballot_sync(kFull, ok);
+    if (!ok) return;
+    const unsigned peers = __match_any_sync(live, cell);
+    const int leader = __ffs(peers) - 1;
+    int first = 0;
+    if (lane == leader) first = atomicAdd(count + cell, __popc(peers));
+    first = __shfl_sync(live, first, leader);
     keys[i] = ((unsigned long long)cell << (3 * b)) | m;
-    vals[i] = i;
+    place[i] = first + __popc(peers & lanemask_lt());
     if (bad) atomicOr((unsigned long long*)&ctr->err, 1ull);
 }
 
-__global__ void __launch_bounds__(256) k_cell_bounds(const unsigned long long* __restrict__ keys, int n,
-                                                     int shift, int total_cells, int* __restrict__ cell_start,
-                                                     unsigned long long* check) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p > n) return;
-    const int c_prev = p > 0 ? (int)(keys[p - 1] >> shift) : -1;
-    const int c_cur = p < n ? (int)(keys[p] >> shift) : total_cells;
-    if (!SR_BOUND(c_prev >= -1 && c_cur <= total_cells, check, kChkCellBounds)) return;
-    for (int c = c_prev + 1; c <= c_cur; ++c) cell_start[c] = p;
+// Cell starts and chunk starts from the counts (both exclusive scans, cell
+// total_cells holding the totals), the chunk -> cell map, and the lists of
+// cells to sort by block.  A tile of 2048 cells per block; the tile's
+// prefix comes from the tiles before it by a decoupled look-back over
+// words holding (flag, particle sum, chunk sum) in (2, 31, 31) bits.
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan(
+    const int* __restrict__ count, int tc, int C, int* __restrict__ cell_start, int* __restrict__ ccs,
+    int* __restrict__ chunk_cell, long long max_chunks, int* __restrict__ huge, long long huge_cap,
+    int4* __restrict__ wsegs, long long wseg_cap, int4* __restrict__ bsegs, long long bseg_cap, int sort_bits,
+    BinCounters* bc, unsigned long long* status, long long* err, unsigned long long* check) {
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_tile;
+    __shared__ unsigned s_wa[kWarps], s_wb[kWarps];
+    __shared__ unsigned s_pa, s_pb;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&bc->tile, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long c0 = (long long)tile * kCellTile + (long long)threadIdx.x * kScanItems;
+    int cnt[kScanItems];
+    unsigned a = 0u, nb = 0u;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const long long c = c0 + k;
+        cnt[k] = c < tc ? count[c] : 0;
+        a += (unsigned)cnt[k];
+        nb += (unsigned)((cnt[k] + C - 1) / C);
+    }
+    unsigned ia = a, ibn = nb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned ta = __shfl_up_sync(kFull, ia, o), tb = __shfl_up_sync(kFull, ibn, o);
+        if (lane >= o) {
+            ia += ta;
+            ibn += tb;
+        }
+    }
+    if (lane == 31) {
+        s_wa[warp] = ia;
+        s_wb[warp] = ibn;
+    }
+    __syncthreads();
+    unsigned wa = 0u, wb = 0u, ta = 0u, tb = 0u;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        if (w < warp) {
+            wa += s_wa[w];
+            wb += s_wb[w];
+        }
+        ta += s_wa[w];
+        tb += s_wb[w];
+    }
+    if (warp == 0) {
+        unsigned long long pa = 0ull, pb = 0ull;
+        const unsigned long long own = ((unsigned long long)ta << 31) | tb;
+        if (tile == 0) {
+            if (lane == 0) st_relaxed(status, kLbPrefix | own);
+        } else {
+            if (lane == 0) st_relaxed(status + tile, kLbAggregate | own);
+            int j = tile - 1, spins = 0;
+            while (true) {
+                const int at = j - lane;
+                const unsigned long long w = at >= 0 ? ld_relaxed(status + at) : kLbPrefix;
+                const unsigned fl = (unsigned)(w >> 62);
+                const unsigned pre = __ballot_sync(kFull, fl == 2u);
+                const unsigned notr = __ballot_sync(kFull, fl == 0u);
+                const int stop = pre ? __ffs(pre) - 1 : 31;             // lanes 0..stop are needed
+                const unsigned need = stop == 31 ? kFull : ((2u << stop) - 1u);
+                if (notr & need) {                                       // a needed tile has not published
+                    if (++spins > kLbMaxSpins) {
+                        if (lane == 0 && err) atomicOr((unsigned long long*)err, 2ull);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                const unsigned va = lane <= stop ? (unsigned)((w >> 31) & 0x7fffffffull) : 0u;
+                const unsigned vb = lane <= stop ? (unsigned)(w & 0x7fffffffull) : 0u;
+                pa += __reduce_add_sync(kFull, va);
+                pb += __reduce_add_sync(kFull, vb);
+                if (pre) break;
+                j -= 32;
+            }
+            if (lane == 0) st_relaxed(status + tile, kLbPrefix | ((pa + ta) << 31) | (pb + tb));
+        }
+        if (lane == 0) {
+            s_pa = (unsigned)pa;
+            s_pb = (unsigned)pb;
+        }
+    }
+    __syncthreads();
+    unsigned ra = s_pa + wa + ia - a, rb = s_pb + wb + ibn - nb;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const long long c = c0 + k;
+        if (c > tc) break;
+        cell_start[c] = (int)ra;
+        ccs[c] = (int)rb;
+        if (c == tc) break;
+        const int m = cnt[k], nch = (m + C - 1) / C;
+        for (int j = 0; j < nch; ++j)
+            if (SR_BOUND((long long)rb + j < max_chunks, check, kChkBinScan)) chunk_cell[rb + j] = (int)c;
+        if (m > kSegTile) {
+            const int h = atomicAdd(&bc->n_huge, 1);
+            if (SR_BOUND(h < huge_cap, check, kChkBinScan)) huge[h] = (int)c;
+        } else if (m > kWarpSeg) {
+            const int s = atomicAdd(&bc->n_bseg, 1);
+            if (SR_BOUND(s < bseg_cap, check, kChkBinScan)) bsegs[s] = make_int4((int)ra, m, 0, sort_bits);
+        } else if (m > 1) {
+            const int s = atomicAdd(&bc->n_wseg, 1);
+            if (SR_BOUND(s < wseg_cap, check, kChkBinScan)) wsegs[s] = make_int4((int)ra, m, 0, sort_bits);
+        }
+        ra += (unsigned)m;
+        rb += (unsigned)nch;
+    }
 }
 
-__global__ void __launch_bounds__(256) k_cell_nch(const int* __restrict__ cell_start, int total_cells,
-                                                  int chunk, int* __restrict__ nch) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > total_cells) return;
-    nch[c] = c < total_cells ? (cell_start[c + 1] - cell_start[c] + chunk - 1) / chunk : 0;
+// Each particle's composite (morton << ib) | caller index at its place in
+// its cell's range.
+__global__ void __launch_bounds__(256) k_scatter(const unsigned long long* __restrict__ keys,
+                                                 const int* __restrict__ place, int n, int b, int ib,
+                                                 const int* __restrict__ cell_start, int tc,
+                                                 unsigned long long* __restrict__ comp, unsigned long long* check) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long k = keys[i];
+    const long long cell = (long long)(k >> (3 * b));
+    if (!SR_BOUND(cell < tc, check, kChkScatter)) return;
+    const long long dest = (long long)cell_start[cell] + place[i];
+    if (!SR_BOUND(dest >= 0 && dest < n, check, kChkScatter)) return;
+    comp[dest] = ((k & ((1ull << (3 * b)) - 1ull)) << ib) | (unsigned long long)i;
 }
 
-// chunk -> cell map: thread per cell writes its chunk range.
-__global__ void __launch_bounds__(256) k_chunk_cell(const int* __restrict__ ccs, int total_cells,
-                                                    int* __restrict__ chunk_cell) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= total_cells) return;
-    for (int k = ccs[c]; k < ccs[c + 1]; ++k) chunk_cell[k] = c;
+// Huge cells, one block each (work queue): buckets on the composite's top 8
+// bits (counted, then placed into scratch at the cell's offsets, both with
+// warp-aggregated shared-memory atomics); buckets of more than one value
+// are listed for k_sort_segments.  Bucket members share the top bits, so a
+// bucket is sorted on the bits below them.
+__global__ void __launch_bounds__(kSplitThreads) k_split(unsigned long long* __restrict__ comp,
+                                                         unsigned long long* __restrict__ scratch,
+                                                         const int* __restrict__ cell_start,
+                                                         const int* __restrict__ huge, BinCounters* bc,
+                                                         int4* __restrict__ wsegs, long long wseg_cap,
+                                                         int4* __restrict__ bsegs, long long bseg_cap, int bits,
+                                                         int n, unsigned long long* check) {
+    __shared__ int hist[256], first[256], fill[256];
+    __shared__ int warp_tot[8];
+    __shared__ int s_item;
+    const int top = bits > 8 ? bits - 8 : 0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&bc->next_huge, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= bc->n_huge) break;
+        const int c = huge[item];
+        const int base = cell_start[c], m = cell_start[c + 1] - base;
+        const int mm = SR_BOUND(base >= 0 && m >= 0 && (long long)base + m <= n, check, kChkBinSort) ? m : 0;
+        if (threadIdx.x < 256) hist[threadIdx.x] = 0;
+        __syncthreads();
+        for (int e0 = warp * 32; e0 < mm; e0 += kSplitThreads) {
+            const int e = e0 + lane;
+            const bool ok = e < mm;
+            const int d = ok ? (int)((comp[base + e] >> top) & 255ull) : 0;
+            warp_add(hist, d, ok);
+        }
+        __syncthreads();
+        // exclusive scan over the 256 buckets by the first 8 warps
+        int ex = 0;
+        if (threadIdx.x < 256) {
+            const int h = hist[threadIdx.x];
+            int x = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += t;
+            }
+            if (lane == 31) warp_tot[warp] = x;
+            ex = x - h;
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            int before = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) before += w < warp ? warp_tot[w] : 0;
+            first[threadIdx.x] = before + ex;
+            fill[threadIdx.x] = before + ex;
+        }
+        __syncthreads();
+        for (int e0 = warp * 32; e0 < mm; e0 += kSplitThreads) {
+            const int e = e0 + lane;
+            const bool ok = e < mm;
+            const unsigned long long v = ok ? comp[base + e] : 0ull;
+            const int at = warp_add(fill, (int)((v >> top) & 255ull), ok);
+            if (ok) scratch[base + at] = v;
+        }
+        __syncthreads();
+        // buckets: one value goes straight back, the rest are listed (a
+        // bucket per thread of the first 8 warps)
+        if (threadIdx.x < 256 && mm > 0) {
+            const int sz = hist[threadIdx.x], o = base + first[threadIdx.x];
+            if (sz == 1) {
+                comp[o] = scratch[o];
+            } else if (sz > 1 && sz <= kWarpSeg) {
+                const int k = atomicAdd(&bc->n_wseg, 1);
+                if (SR_BOUND(k < wseg_cap, check, kChkBinSort)) wsegs[k] = make_int4(o, sz, 1, top);
+            } else if (sz > kWarpSeg) {
+                const int k = atomicAdd(&bc->n_bseg, 1);
+                if (SR_BOUND(k < bseg_cap, check, kChkBinSort)) bsegs[k] = make_int4(o, sz, 1, top);
+            }
+        }
+        __syncthreads();
+    }
 }
 
-// One warp per chunk of C = 32 K slots (lane l fills slots l + 32 s):
-// slot positions / indices, anchor, bounding box.  active (caller order,
-// nullable = every particle active) marks the particles whose forces are
-// wanted: slot w = 1 (active), -1 (passive, a neighbour only) or 0 (empty);
-// chunk_hi.w = the chunk's count of active particles (int bits).
+// One stable LSD pass on the digit at `shift` of src[0, m) into dst (dst
+// may be src when m <= kSegTile: every value is in registers before the
+// first write).  run[d]: the digit's first destination, advanced past
+// each tile.  Warp w takes a contiguous part of each tile, 32 at a time,
+// so ties keep their order.
+__device__ void seg_pass(const unsigned long long* src, unsigned long long* dst, int m, int shift, int* run,
+                         int (*wh)[256], unsigned long long* check) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    for (int t0 = 0; t0 < m; t0 += kSegTile) {
+        const int tm = min(kSegTile, m - t0);
+        const int per = (tm + kSegThreads - 1) / kSegThreads * 32;     // elements per warp
+        for (int i = threadIdx.x; i < kSegWarps * 256; i += kSegThreads) (&wh[0][0])[i] = 0;
+        __syncthreads();
+        unsigned long long v[kSegRounds];
+        int dg[kSegRounds], rk[kSegRounds];
+#pragma unroll
+        for (int r = 0; r < kSegRounds; ++r) {
+            v[r] = 0ull;
+            dg[r] = 256;
+            rk[r] = 0;
+            if (r * 32 < per) {
+                const int e = warp * per + r * 32 + lane;
+                const bool ok = e < tm;
+                if (ok) {
+                    v[r] = src[t0 + e];
+                    dg[r] = (int)((v[r] >> shift) & 255ull);
+                }
+                const unsigned peers = __match_any_sync(kFull, dg[r]);
+                const int old = ok ? wh[warp][dg[r]] : 0;
+                __syncwarp();
+                if (ok && lane == __ffs(peers) - 1) wh[warp][dg[r]] = old + __popc(peers);
+                __syncwarp();
+                rk[r] = old + __popc(peers & lt);
+            }
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;                 // one digit per thread
+            int acc = run[d];
+#pragma unroll
+            for (int w = 0; w < kSegWarps; ++w) {
+                const int t = wh[w][d];
+                wh[w][d] = acc;
+                acc += t;
+            }
+            run[d] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSegRounds; ++r)
+            if (dg[r] < 256) {
+                const int at = wh[warp][dg[r]] + rk[r];
+                if (SR_BOUND(at >= 0 && at < m, check, kChkBinSort)) dst[at] = v[r];
+            }
+        __syncthreads();
+    }
+}
+
+// The listed ranges, sorted by the low `bits` bits into the composites
+// array (from it, or from scratch where the split left a bucket).  First
+// the warp list, one warp per range (dealt round robin): bitonic in registers up
+// to kSmallCell, else warp_lsd in the warp's part of shared memory.  Then
+// the block list, one block per range: a stable LSD sort on 8-bit digits,
+// in shared memory up to kSegTile values, else through the composites and
+// scratch arrays in turn; passes whose digit is the same for the whole
+// range are skipped.
+__global__ void __launch_bounds__(kSegThreads) k_sort_segments(unsigned long long* __restrict__ comp,
+                                                               unsigned long long* __restrict__ scratch,
+                                                               const int4* __restrict__ wsegs,
+                                                               const int4* __restrict__ bsegs, BinCounters* bc,
+                                                               int n, unsigned long long* check) {
+    extern __shared__ unsigned long long sv[];   // see kSortSmem
+    int (*hist)[256] = reinterpret_cast<int (*)[256]>(sv + kSegTile);   // block phase only
+    __shared__ int wh[kSegWarps][256];
+    __shared__ int run[256];
+    __shared__ int warp_tot[8];
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // warp list: items dealt round robin to the grid's warps, the next
+    // item's entry loaded while the current one is sorted
+    const int n_w = bc->n_wseg, stride = gridDim.x * kSegWarps;
+    int item = blockIdx.x * kSegWarps + warp;
+    int4 sg = item < n_w ? wsegs[item] : make_int4(0, 0, 0, 0);
+    while (item < n_w) {
+        const int next = item + stride;
+        const int4 sn = next < n_w ? wsegs[next] : make_int4(0, 0, 0, 0);
+        if (SR_BOUND(sg.x >= 0 && sg.y >= 0 && sg.y <= kWarpSeg && (long long)sg.x + sg.y <= n && sg.w >= 0 &&
+                         sg.w <= 64,
+                     check, kChkBinSort)) {
+            const unsigned long long* src = (sg.z ? scratch : comp) + sg.x;
+            if (sg.y <= kSmallCell) warp_sort_small(src, comp + sg.x, sg.y);
+            else warp_lsd(src, comp + sg.x, sg.y, sg.w, sv + 2 * warp * kWarpSeg, wh[warp]);
+        }
+        item = next;
+        sg = sn;
+    }
+    __syncthreads();
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&bc->next_bseg, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= bc->n_bseg) break;
+        const int4 sg = bsegs[item];
+        const int off = sg.x, m = sg.y, bits = sg.w;
+        const bool ok = SR_BOUND(off >= 0 && m >= 0 && (long long)off + m <= n && bits >= 0 && bits <= 64,
+                                 check, kChkBinSort);
+        const int passes = ok ? (bits + 7) / 8 : 0;
+        const int mm = ok ? m : 0;
+        unsigned long long* home = comp + off;
+        const unsigned long long* src = (sg.z ? scratch : comp) + off;
+        for (int i = threadIdx.x; i < kSegMaxPasses * 256; i += kSegThreads) (&hist[0][0])[i] = 0;
+        __syncthreads();
+        for (int e0 = warp * 32; e0 < mm; e0 += kSegThreads) {
+            const int e = e0 + lane;
+            const bool in = e < mm;
+            const unsigned long long v = in ? src[e] : 0ull;
+            for (int p = 0; p < passes; ++p) warp_add(hist[p], (int)((v >> (8 * p)) & 255ull), in);
+        }
+        __syncthreads();
+        const bool in_smem = mm <= kSegTile;
+        unsigned long long* cur = in_smem ? sv : const_cast<unsigned long long*>(src);
+        unsigned long long* nxt = in_smem ? sv : (sg.z ? comp : scratch) + off;
+        if (in_smem)
+            for (int e = threadIdx.x; e < mm; e += kSegThreads) sv[e] = src[e];
+        __syncthreads();
+        for (int p = 0; p < passes; ++p) {
+            const int h = hist[p][threadIdx.x];
+            if (__syncthreads_or(h == mm)) continue;             // one digit throughout: order kept
+            run[threadIdx.x] = block_exclusive_scan256(h, warp_tot);
+            __syncthreads();
+            seg_pass(cur, nxt, mm, 8 * p, run, wh, check);
+            if (!in_smem) {
+                unsigned long long* t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+        }
+        if (ok && cur != home)
+            for (int e = threadIdx.x; e < mm; e += kSegThreads) home[e] = cur[e];
+        __syncthreads();
+    }
+}
+
+// One chunk: slot offsets, indices and flags, anchor, bounding box and
+// counts from the caller indices of its slots (lane l holds slots l + 32 s).
+template <int K>
+__device__ __forceinline__ void fill_chunk(
+    long long k, int cell, const int (&idx_in)[K], const bool (&valid_in)[K], int cnt,
+    const double* __restrict__ pos, const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base,
+    int n_vol, float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
+    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, const unsigned char* __restrict__ active, int n,
+    unsigned long long* check) {
+    constexpr int C = 32 * K;
+    const int lane = threadIdx.x & 31;
+    const int v = n_vol > 1 ? volume_of_cell(cell, vol_cell_base, n_vol) : 0;
+    const VolDev& V = vols[v];
+    int orig[K], q[K][3], F[K][3];
+    unsigned long long mant[K][3];
+    double t[K][3];
+    bool valid[K], fast[K];
+    const unsigned long long ubox = (unsigned long long)__double_as_longlong(V.box);
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        valid[s] = valid_in[s];
+        fast[s] = false;
+        orig[s] = -1;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) { q[s][ax] = 0; t[s][ax] = 0.0; F[s][ax] = -1; mant[s][ax] = 0ull; }
+        if (valid[s]) {
+            orig[s] = idx_in[s];
+            if (!SR_BOUND(orig[s] >= 0 && orig[s] < n, check, kChkChunkFill)) orig[s] = 0;
+            const double x3[3] = {pos[3ll * orig[s]], pos[3ll * orig[s] + 1], pos[3ll * orig[s] + 2]};
+            // the integer path needs t >= 1 on every axis for the offsets;
+            // q holds the unclamped floor(t) there (the anchor is clamped)
+            bool f = true;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+                f = f && (V.h_pow2 ? fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[s][ax], mant[s][ax], F[s][ax])
+                                   : fine_axis_quot(x3[ax], ubox, V.h, V.inv_h, q[s][ax], mant[s][ax],
+                                                    F[s][ax])) &&
+                    F[s][ax] >= 0;
+            fast[s] = f;
+            if (!f) {
+                bool bad = false;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) fine_axis(x3[ax], V, t[s][ax], q[s][ax], bad);
+            }
+        }
+    }
+    int nact = 0;
+#pragma unroll
+    for (int s = 0; s < K; ++s) nact += __popc(__ballot_sync(kFull, valid[s] && (!active || active[orig[s]])));
+    int qa[3];
+    float bl[3], bh[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        qa[ax] = min(__shfl_sync(kFull, q[0][ax], 0), V.M - 1);   // slot 0 always exists
+        bl[ax] = __int_as_float(0x7f800000);          // +inf
+        bh[ax] = __int_as_float(0xff800000);          // -inf
+    }
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        float off[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            off[ax] = !valid[s] ? kPad
+                      : fast[s] ? offset_bits(mant[s][ax], F[s][ax], q[s][ax], qa[ax])
+                                : __double2float_rn(t[s][ax] - (double)qa[ax]);
+            if (valid[s]) {
+                bl[ax] = fminf(bl[ax], off[ax]);
+                bh[ax] = fmaxf(bh[ax], off[ax]);
+            }
+        }
+        const long long slot = (long long)k * C + lane + 32 * s;
+        const float w = !valid[s] ? 0.0f : (!active || active[orig[s]]) ? 1.0f : -1.0f;
+        slot_pos[slot] = make_float4(off[0], off[1], off[2], w);
+        slot_idx[slot] = orig[s];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            bl[ax] = fminf(bl[ax], __shfl_xor_sync(kFull, bl[ax], o));
+            bh[ax] = fmaxf(bh[ax], __shfl_xor_sync(kFull, bh[ax], o));
+        }
+    }
+    if (lane == 0) {
+        chunk_meta[k] = make_int4(qa[0], qa[1], qa[2], v);
+        chunk_lo[k] = make_float4(bl[0], bl[1], bl[2], __int_as_float(cnt));
+        chunk_hi[k] = make_float4(bh[0], bh[1], bh[2], __int_as_float(nact));
+    }
+}
+
+// One warp per chunk: the caller indices of its slots from the sorted
+// composites, then the chunk's slots and records; perm[sorted position] =
+// caller index.
 template <int K>
 __global__ void __launch_bounds__(256) k_chunk_fill(
-    const double* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ cell_start,
-    const int* __restrict__ ccs, const int* __restrict__ chunk_cell, int total_cells,
-    const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base, int n_vol,
+    const double* __restrict__ pos, const unsigned long long* __restrict__ comp, int ib,
+    const int* __restrict__ cell_start, const int* __restrict__ ccs, const int* __restrict__ chunk_cell,
+    int total_cells, const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base, int n_vol,
     float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
-    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, const unsigned char* __restrict__ active,
-    int n, long long max_chunks, unsigned long long* check) {
+    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, int* __restrict__ perm,
+    const unsigned char* __restrict__ active, int n, long long max_chunks, unsigned long long* check) {
     constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
     const int n_chunks = ccs[total_cells];
     const int warps = gridDim.x * (blockDim.x >> 5);
+    const unsigned long long imask = (1ull << ib) - 1ull;
     for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_chunks; k += warps) {
         const int cell = chunk_cell[k];
         if (!SR_BOUND(k < max_chunks && cell >= 0 && cell < total_cells, check, kChkChunkFill)) continue;
-        const int r0 = (k - ccs[cell]) * C;
-        const int n_cell = cell_start[cell + 1] - cell_start[cell];
-        const int v = n_vol > 1 ? volume_of_cell(cell, vol_cell_base, n_vol) : 0;
-        const VolDev& V = vols[v];
-        int orig[K], q[K][3], F[K][3];
-        unsigned long long mant[K][3];
-        double t[K][3];
-        bool valid[K], fast[K];
-        const unsigned long long ubox = (unsigned long long)__double_as_longlong(V.box);
+        const int base = cell_start[cell];
+        const int m = max(0, cell_start[cell + 1] - base);
+        const int kc = k - ccs[cell];
+        if (!SR_BOUND(base >= 0 && (long long)base + m <= n && kc >= 0, check, kChkChunkFill)) continue;
+        int idx[K];
+        bool valid[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-            const int rank = r0 + lane + 32 * s;
-            valid[s] = rank < n_cell;
-            fast[s] = false;
-            orig[s] = -1;
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) { q[s][ax] = 0; t[s][ax] = 0.0; F[s][ax] = -1; mant[s][ax] = 0ull; }
-            if (valid[s] && !SR_BOUND(cell_start[cell] + rank < n, check, kChkChunkFill)) valid[s] = false;
+            const int e = kc * C + lane + 32 * s;
+            valid[s] = e < m;
+            idx[s] = -1;
             if (valid[s]) {
-                orig[s] = perm[cell_start[cell] + rank];
-                if (!SR_BOUND(orig[s] >= 0 && orig[s] < n, check, kChkChunkFill)) orig[s] = 0;
-                const double x3[3] = {pos[3ll * orig[s]], pos[3ll * orig[s] + 1], pos[3ll * orig[s] + 2]};
-                // the integer path needs t >= 1 on every axis for the offsets;
-                // q holds the unclamped floor(t) there (the anchor is clamped)
-                bool f = true;
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax)
-                    f = f && (V.h_pow2 ? fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[s][ax], mant[s][ax], F[s][ax])
-                                       : fine_axis_quot(x3[ax], ubox, V.h, V.inv_h, q[s][ax], mant[s][ax],
-                                                        F[s][ax])) &&
-                        F[s][ax] >= 0;
-                fast[s] = f;
-                if (!f) {
-                    bool bad = false;
-#pragma unroll
-                    for (int ax = 0; ax < 3; ++ax) fine_axis(x3[ax], V, t[s][ax], q[s][ax], bad);
-                }
+                idx[s] = (int)(comp[base + e] & imask);
+                perm[base + e] = idx[s];
             }
         }
-        int nact = 0;
-#pragma unroll
-        for (int s = 0; s < K; ++s) nact += __popc(__ballot_sync(kFull, valid[s] && (!active || active[orig[s]])));
-        int qa[3];
-        float bl[3], bh[3];
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            qa[ax] = min(__shfl_sync(kFull, q[0][ax], 0), V.M - 1);   // slot 0 (rank r0) always exists
-            bl[ax] = __int_as_float(0x7f800000);          // +inf
-            bh[ax] = __int_as_float(0xff800000);          // -inf
-        }
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            float off[3];
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                off[ax] = !valid[s] ? kPad
-                          : fast[s] ? offset_bits(mant[s][ax], F[s][ax], q[s][ax], qa[ax])
-                                    : __double2float_rn(t[s][ax] - (double)qa[ax]);
-                if (valid[s]) {
-                    bl[ax] = fminf(bl[ax], off[ax]);
-                    bh[ax] = fmaxf(bh[ax], off[ax]);
-                }
-            }
-            const long long slot = (long long)k * C + lane + 32 * s;
-            const float w = !valid[s] ? 0.0f : (!active || active[orig[s]]) ? 1.0f : -1.0f;
-            slot_pos[slot] = make_float4(off[0], off[1], off[2], w);
-            slot_idx[slot] = orig[s];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                bl[ax] = fminf(bl[ax], __shfl_xor_sync(kFull, bl[ax], o));
-                bh[ax] = fmaxf(bh[ax], __shfl_xor_sync(kFull, bh[ax], o));
-            }
-        }
-        if (lane == 0) {
-            const int cnt = min(C, n_cell - r0);
-            chunk_meta[k] = make_int4(qa[0], qa[1], qa[2], v);
-            chunk_lo[k] = make_float4(bl[0], bl[1], bl[2], __int_as_float(cnt));
-            chunk_hi[k] = make_float4(bh[0], bh[1], bh[2], __int_as_float(nact));
-        }
+        fill_chunk<K>(k, cell, idx, valid, min(C, m - kc * C), pos, vols, vol_cell_base, n_vol, slot_pos, slot_idx,
+                      chunk_meta, chunk_lo, chunk_hi, active, n, check);
     }
 }
 
 }  // namespace
 
+int bin_alloc(sr_plan* p) {
+    BinScratch& B = p->bin;
+    const long long tc = p->total_cells, cap = p->capacity;
+    const long long tiles = (tc + 1 + kCellTile - 1) / kCellTile;
+    const size_t off_status = 64, off_count = off_status + 8 * (size_t)tiles;
+    B.clear_bytes = off_count + 4 * (size_t)(tc + 1);
+    // list sizes: listed ranges are disjoint, each of at least 2 (warp list),
+    // more than kWarpSeg (block list) or more than kSegTile (huge) elements
+    B.huge_cap = cap / kSegTile + 1;
+    B.bseg_cap = cap / kWarpSeg + 1;
+    B.wseg_cap = cap / 2 + 1;
+    cudaError_t e = cudaMalloc(&B.region, B.clear_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&B.huge, sizeof(int) * (size_t)B.huge_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&B.wsegs, sizeof(int4) * (size_t)B.wseg_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&B.bsegs, sizeof(int4) * (size_t)B.bseg_cap);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "bin_alloc");
+    char* r = static_cast<char*>(B.region);
+    B.counters = reinterpret_cast<BinCounters*>(r);
+    B.status = reinterpret_cast<unsigned long long*>(r + off_status);
+    B.count = reinterpret_cast<int*>(r + off_count);
+    return SR_OK;
+}
+
+void bin_free(sr_plan* p) {
+    BinScratch& B = p->bin;
+    cudaFree(B.region);
+    cudaFree(B.huge);
+    cudaFree(B.wsegs);
+    cudaFree(B.bsegs);
+    B = BinScratch{};
+}
+
 int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, const unsigned char* active) {
+    BinScratch& B = p->bin;
     const int b = p->sub_bits;
     const int ni = (int)n;
+    const int tc = (int)p->total_cells;
+    const int C = 32 * p->chunk_k;
+    int ib = 1;                                   // bits of a caller index: n - 1 < 2^ib
+    while ((1ll << ib) < n) ++ib;
+    const int bits = 3 * b + ib;
+    unsigned long long* check = &p->ctr->check;
+    SR_CUDA_CHECK(cudaMemsetAsync(B.region, 0, B.clear_bytes, st));
     if (ni > 0) {
-        k_keys<<<(ni + 255) / 256, 256, 0, st>>>(pos, ni, p->vols, p->vol_part_start, p->n_vol, b,
-                                                 p->keys[0], p->vals[0], p->ctr);
+        k_keys<<<(ni + 255) / 256, 256, 0, st>>>(pos, ni, p->vols, p->vol_part_start, p->n_vol, b, p->keys[0],
+                                                 p->vals[0], B.count, p->ctr);
         SR_LAUNCH_CHECK("k_keys");
     }
-    int which = 0;
-    int rc = radix_sort_pairs(p->keys, p->vals, ni, p->key_bits, p->rs_particles, st, &which, &p->ctr->check,
-                              &p->ctr->err);
-    if (rc) return rc;
-    p->sorted = which;
-    const int tc = (int)p->total_cells;
-    k_cell_bounds<<<(ni + 1 + 255) / 256, 256, 0, st>>>(p->keys[which], ni, 3 * b, tc, p->cell_start,
-                                                        &p->ctr->check);
-    SR_LAUNCH_CHECK("k_cell_bounds");
-    k_cell_nch<<<(tc + 1 + 255) / 256, 256, 0, st>>>(p->cell_start, tc, 32 * p->chunk_k, p->cell_nch);
-    SR_LAUNCH_CHECK("k_cell_nch");
-    rc = exclusive_scan(p->cell_nch, p->ccs, tc + 1, p->scan_cells, st);
-    if (rc) return rc;
-    k_chunk_cell<<<(tc + 255) / 256, 256, 0, st>>>(p->ccs, tc, p->chunk_cell);
-    SR_LAUNCH_CHECK("k_chunk_cell");
+    const int tiles = (tc + 1 + kCellTile - 1) / kCellTile;
+    k_cell_scan<<<tiles, kScanThreads, 0, st>>>(B.count, tc, C, p->cell_start, p->ccs, p->chunk_cell, p->max_chunks,
+                                                B.huge, B.huge_cap, B.wsegs, B.wseg_cap, B.bsegs, B.bseg_cap, bits,
+                                                B.counters, B.status,
+                                                &p->ctr->err, check);
+    SR_LAUNCH_CHECK("k_cell_scan");
+    if (ni > 0) {
+        k_scatter<<<(ni + 255) / 256, 256, 0, st>>>(p->keys[0], p->vals[0], ni, b, ib, p->cell_start, tc, p->keys[1],
+                                                    check);
+        SR_LAUNCH_CHECK("k_scatter");
+        k_split<<<p->sm_count, kSplitThreads, 0, st>>>(p->keys[1], p->keys[0], p->cell_start, B.huge, B.counters,
+                                                       B.wsegs, B.wseg_cap, B.bsegs, B.bseg_cap, bits, ni, check);
+        SR_LAUNCH_CHECK("k_split");
+        k_sort_segments<<<p->sm_count * 4, kSegThreads, kSortSmem, st>>>(p->keys[1], p->keys[0], B.wsegs, B.bsegs,
+                                                                          B.counters, ni, check);
+        SR_LAUNCH_CHECK("k_sort_segments");
+    }
     long long want = (p->max_chunks + 7) / 8;
     long long cap = (long long)p->sm_count * 16;
     const int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     if (p->chunk_k == 2)
-        k_chunk_fill<2><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
-                                                p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
-                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active, ni, p->max_chunks,
-                                                &p->ctr->check);
+        k_chunk_fill<2><<<blocks, 256, 0, st>>>(pos, p->keys[1], ib, p->cell_start, p->ccs, p->chunk_cell, tc, p->vols,
+                                                p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx, p->chunk_meta,
+                                                p->chunk_lo, p->chunk_hi, p->vals[1], active, ni, p->max_chunks,
+                                                check);
     else
-        k_chunk_fill<1><<<blocks, 256, 0, st>>>(pos, p->vals[which], p->cell_start, p->ccs, p->chunk_cell, tc,
-                                                p->vols, p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx,
-                                                p->chunk_meta, p->chunk_lo, p->chunk_hi, active, ni, p->max_chunks,
-                                                &p->ctr->check);
+        k_chunk_fill<1><<<blocks, 256, 0, st>>>(pos, p->keys[1], ib, p->cell_start, p->ccs, p->chunk_cell, tc, p->vols,
+                                                p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx, p->chunk_meta,
+                                                p->chunk_lo, p->chunk_hi, p->vals[1], active, ni, p->max_chunks,
+                                                check);
     SR_LAUNCH_CHECK("k_chunk_fill");
+    p->sorted = 1;
     return launch_cost_and_order(p, st);
 }
 

@@ -28,6 +28,8 @@ enum CheckCode : int {
     kChkChunkFill = 10,   // binning: sorted position, caller row or slot outside its array
     kChkScatter = 11,     // radix scatter: destination outside [0, n)
     kChkCenters = 12,     // center finder: slot or accumulator outside its halo's block
+    kChkBinScan = 13,     // binning cell scan: chunk or list entry outside its table
+    kChkBinSort = 14,     // binning: range to sort outside [0, n), or list over-filled
     kChkSelfTest = 99,    // sr_check_selftest
 };
 
@@ -174,6 +176,35 @@ struct Counters {
     long long reserved;
 };
 
+// Work counters of one binning (bin.cu), cleared with the cell counts
+// before each sr_bin.
+struct BinCounters {
+    unsigned tile;        // next tile of the cell scan
+    int n_huge;           // cells listed for the split
+    int n_wseg;           // ranges listed for a warp sort
+    int n_bseg;           // ranges listed for a block sort
+    int next_huge;        // work-queue positions
+    int next_wseg;
+    int next_bseg;
+    int pad;
+};
+
+// Binning workspace: one region cleared per sr_bin (counters, the cell
+// scan's look-back words, the per-cell counts) and the two work lists.
+struct BinScratch {
+    void* region = nullptr;
+    size_t clear_bytes = 0;
+    BinCounters* counters = nullptr;
+    unsigned long long* status = nullptr;
+    int* count = nullptr;                 // total_cells + 1
+    int* huge = nullptr;                  // cells to split
+    long long huge_cap = 0;
+    int4* wsegs = nullptr;                // ranges to sort by warp: offset, size, source (1 = scratch), key bits
+    long long wseg_cap = 0;
+    int4* bsegs = nullptr;                // ranges to sort by block, same fields
+    long long bseg_cap = 0;
+};
+
 struct ScanScratch {
     std::vector<int*> partials;   // one buffer per recursion level
     std::vector<int> sizes;
@@ -211,7 +242,6 @@ struct sr_plan {
     int* vals[2] = {nullptr, nullptr};
     int sorted = 0;                        // buffer index holding the sorted result
     int* cell_start = nullptr;             // total_cells + 1
-    int* cell_nch = nullptr;               // total_cells + 1
     int* ccs = nullptr;                    // cell -> first chunk, total_cells + 1
     int* chunk_cell = nullptr;             // chunk -> cell
     int4* chunk_meta = nullptr;            // anchor qx, qy, qz, volume
@@ -226,9 +256,8 @@ struct sr_plan {
     float4* slot_g = nullptr;
     sr::Counters* ctr = nullptr;
     double* inv_partials = nullptr;
-    sr::RadixScratch rs_particles;
     sr::RadixScratch rs_chunks;
-    sr::ScanScratch scan_cells;
+    sr::BinScratch bin;
 
     // captured whole-step graph (sr_graph_capture)
     cudaGraphExec_t graph_exec = nullptr;
@@ -286,6 +315,8 @@ int radix_sort_pairs(unsigned long long* keys[2], int* vals[2], int n, int key_b
                      long long* err = nullptr);
 
 // binning (bin.cu)
+int bin_alloc(sr_plan* p);
+void bin_free(sr_plan* p);
 int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st,
                const unsigned char* active = nullptr);
 

@@ -139,6 +139,50 @@ def test_bin_partial_fill_and_rebin():
         _compare(plan, [(pos, L)])
 
 
+def _cells_of_sizes(sizes, L, n_c, seed, spread=None):
+    """Positions with sizes[k] particles in cell k (cells in x order along
+    the first row; spread: side of the cube inside the cell that holds them,
+    0 = all at one point), shuffled into random caller order."""
+    rng = np.random.default_rng(seed)
+    side = L / n_c
+    parts = []
+    for k, m in enumerate(sizes):
+        w = side if spread is None else spread
+        lo = np.array([k * side, 0.0, 0.0]) + (side - w) / 2
+        parts.append(lo + rng.random((m, 3)) * w)
+    pos = np.concatenate(parts)
+    return pos[rng.permutation(len(pos))]
+
+
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_bin_dense_cells_every_sort_path(chunk):
+    # cells of 0..kSmallCell particles are sorted by one warp in registers,
+    # up to kSegTile in shared memory by one block, larger ones split on
+    # their top bits first (and a bucket still above kSegTile sorted through
+    # global memory); sizes at and next to each threshold, a dense blob,
+    # and coincident positions (a single fine cell: ties on the Morton code
+    # broken by caller index alone)
+    L, n_c = 32.0, 8
+    side = L / n_c
+    sizes = [1, 31, 32, 33, 64, 65, 127, 128]
+    pos_a = _cells_of_sizes(sizes, L, n_c, 51) + [0.0, 2 * side, 0.0]                 # cells (k, 2, 0)
+    pos_b = _cells_of_sizes([129, 200, 1000, 2047, 2048, 2049, 9000, 0], L, n_c, 52)  # cells (k, 0, 0)
+    blob = _cells_of_sizes([0, 0, 20000], L, n_c, 53, spread=0.05) + [0.0, 0.0, 3 * side]   # a few fine cells
+    same = np.tile([[3.375 * side, 3.375 * side, 0.375 * side]], (6000, 1))             # one point
+    rest = gen.uniform_box(5000, L, 54) * [1.0, 1.0, 3 * side / L] + [0.0, 0.0, 5 * side]   # z cells 5..7
+    pos = np.concatenate([pos_a, pos_b, blob, same, rest])
+    pos = pos[np.random.default_rng(55).permutation(len(pos))]
+    vols = [(pos, L)]
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), n_cells=[n_c], chunk_size=chunk)
+    _compare(plan, vols)
+    plan.status()
+    # the same particles again: the atomics' order changes, the result not
+    first = [to_np(plan.export(k)).copy() for k in ("perm", "slot_pos", "slot_idx")]
+    plan.bin(torch.from_numpy(pos).cuda())
+    for a, k in zip(first, ("perm", "slot_pos", "slot_idx")):
+        assert a.tobytes() == to_np(plan.export(k)).tobytes()
+
+
 @pytest.mark.parametrize("sub_bits,chunk", [(6, 32), (3, 64), (6, 64)])
 def test_bin_power_of_two_side_with_sub_cells(sub_bits, chunk):
     # box 32, 8 cells: h = 4 / 2^b is a power of two (the integer path of the

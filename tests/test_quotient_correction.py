@@ -67,3 +67,42 @@ def test_single_correction_is_not_enough():
         if abs(Fr(x * y) - q) >= Fr(math.ulp(float(q))):
             far += 1
     assert far > 0
+
+
+def _floor_from_product(x, y):
+    """The keys kernel's shortcut: floor(x / h) from the one product t' = x y,
+    or None where t' lies within 16 ulps of an integer (the kernel then takes
+    the corrected quotient)."""
+    t = x * y
+    if t < 1.0:
+        return None if t >= 1.0 - 16 * 2.0 ** -53 else 0
+    q = math.floor(t)
+    u = math.ulp(t)
+    if t - q < 16 * u or (q + 1) - t <= 16 * u:
+        return None
+    return q
+
+
+def test_floor_from_one_product_matches_the_division():
+    # the shortcut's premise: t' = RN(x RN(1/h)) lies within 2.5 ulp of
+    # RN(x / h), so away from integers (16 ulps) floor(t') = floor(x / h);
+    # checked on random positions and on positions a few ulps either side of
+    # the faces k h, where the shortcut must decline
+    rng = np.random.default_rng(77)
+    boxes = [23.0, 98.0, 17.0, 30.0, 1000.0 / 3.0, 0.7, 3.3e5] + list(rng.uniform(6.0, 600.0, 5))
+    taken = declined = 0
+    for box in boxes:
+        for M in (max(1, int(box // 4)) << 6, 13, 1000):
+            h, xs = _cases(rng, box, M)
+            y = float(1 / Fr(h))
+            for x in xs:
+                exact = Fr(x) / Fr(h)
+                t_rn = float(exact)                               # RN(x / h)
+                assert abs(Fr(x * y) - Fr(t_rn)) <= Fr(5, 2) * Fr(math.ulp(t_rn))
+                q = _floor_from_product(x, y)
+                if q is None:
+                    declined += 1
+                    continue
+                taken += 1
+                assert q == math.floor(t_rn), (box, M, x)
+    assert taken > 15000 and declined > 500
