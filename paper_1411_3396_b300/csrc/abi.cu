@@ -42,7 +42,7 @@ void free_plan(sr_plan* p) {
     }
     cudaFree(p->cell_start);
     cudaFree(p->ccs);
-    cudaFree(p->chunk_cell);
+    cudaFree(p->chunk_span);
     cudaFree(p->chunk_meta);
     cudaFree(p->chunk_lo);
     cudaFree(p->chunk_hi);
@@ -210,7 +210,7 @@ int build_plan(const sr_params* params, const long long* n, int n_vol, bool batc
     }
     SR_ALLOC(p->cell_start, cells + 1);
     SR_ALLOC(p->ccs, cells + 1);
-    SR_ALLOC(p->chunk_cell, mc);
+    SR_ALLOC(p->chunk_span, mc);
     SR_ALLOC(p->chunk_meta, mc);
     SR_ALLOC(p->chunk_lo, mc);
     SR_ALLOC(p->chunk_hi, mc);

@@ -19,7 +19,8 @@
 //                    taken with atomics give each particle a place in its
 //                    cell (in no fixed order)
 //   k_cell_scan      one pass over the cells (decoupled look-back): cell
-//                    starts, chunk starts and the chunk -> cell map; cells
+//                    starts, chunk starts and each chunk's record (cell,
+//                    first sorted row, count, volume); cells
 //                    of 2..kWarpSeg particles are listed for a warp sort,
 //                    larger ones up to kSegTile for a block sort, the rest
 //                    as huge
@@ -27,11 +28,12 @@
 //   k_split          one block per huge cell splits it on the composite's
 //                    top 8 bits into up to 256 buckets, which are listed
 //   k_sort_segments  the listed ranges: a warp each (bitonic in registers
-//                    up to kSmallCell, else a stable LSD sort on 8-bit
-//                    digits in the warp's shared memory), then a block each
-//                    for the block list (the same LSD sort, through global
-//                    memory above kSegTile)
-//   k_chunk_fill     one warp per chunk: slots from the sorted composites
+//                    up to kSmallCell, else stable LSD passes on the
+//                    Morton code's 8-bit digits in the warp's shared memory
+//                    and then each run of equal codes in caller-index
+//                    order), then a block each for the block list (the same
+//                    steps, through global memory above kSegTile)
+//   k_chunk_fill     one warp per U chunks: slots from the sorted composites
 // The composites of a cell are distinct (the caller index is part of
 // them), so each cell ends in the spec's order whatever order the atomics
 // left, and the result is a pure function of the input.
@@ -185,12 +187,16 @@ constexpr int kSegThreads = 256;                // one 8-bit digit per thread
 constexpr int kSegWarps = kSegThreads / 32;
 constexpr int kSegRounds = kSegTile / kSegThreads;
 constexpr int kSegMaxPasses = 8;                // composites of up to 64 bits
+constexpr int kTieRunMax = 32;                 // longest run of equal Morton codes fixed by one thread
 // k_sort_segments' dynamic shared memory: two kWarpSeg halves per warp in
 // the warp phase; kSegTile values and the pass histograms in the block phase
 constexpr int kSortSmem = (int)sizeof(unsigned long long) * 2 * kSegWarps * kWarpSeg;
 static_assert(sizeof(unsigned long long) * kSegTile + sizeof(int) * kSegMaxPasses * 256 <= (size_t)kSortSmem,
               "block phase fits in the warp phase's shared memory");
 constexpr int kSplitThreads = 512;
+constexpr int kSplitRounds = 8;                // elements per thread per round of k_split (loads in flight)
+constexpr int kFillU1 = 2;                     // chunks per warp round of k_chunk_fill (32-slot chunks)
+constexpr int kFillU2 = 2;                     // (64-slot chunks)
 constexpr int kCellTile = kScanTile;            // cells per block of the cell scan
 constexpr unsigned long long kLbAggregate = 1ull << 62;   // look-back word: the tile's own sums
 constexpr unsigned long long kLbPrefix = 2ull << 62;      // look-back word: inclusive prefix
@@ -248,23 +254,31 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[S]) {
     }
 }
 
-// One warp sorts src[0, m) (m <= 32 S) into dst[0, m) (dst may be src).
+// The values of a range of at most kSmallCell (lane l: elements l + 32 s,
+// ~0 past the end), loaded ahead of its sort; nothing for larger ranges.
+__device__ __forceinline__ void load_small(const unsigned long long* src, int m, unsigned long long (&v)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) v[s] = m <= kSmallCell && lane + 32 * s < m ? src[lane + 32 * s] : ~0ull;
+}
+
 template <int S>
-__device__ __forceinline__ void warp_sort_copy(const unsigned long long* src, unsigned long long* dst, int m) {
+__device__ __forceinline__ void warp_sort_store_s(const unsigned long long (&in)[4], unsigned long long* dst, int m) {
     const int lane = threadIdx.x & 31;
     unsigned long long v[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) v[s] = lane + 32 * s < m ? src[lane + 32 * s] : ~0ull;
+    for (int s = 0; s < S; ++s) v[s] = in[s];
     warp_bitonic<S>(v);
 #pragma unroll
     for (int s = 0; s < S; ++s)
         if (lane + 32 * s < m) dst[lane + 32 * s] = v[s];
 }
 
-__device__ __forceinline__ void warp_sort_small(const unsigned long long* src, unsigned long long* dst, int m) {
-    if (m <= 32) warp_sort_copy<1>(src, dst, m);
-    else if (m <= 64) warp_sort_copy<2>(src, dst, m);
-    else warp_sort_copy<4>(src, dst, m);
+// Sorts the preloaded values of a range of m <= kSmallCell into dst.
+__device__ __forceinline__ void warp_sort_store(const unsigned long long (&v)[4], unsigned long long* dst, int m) {
+    if (m <= 32) warp_sort_store_s<1>(v, dst, m);
+    else if (m <= 64) warp_sort_store_s<2>(v, dst, m);
+    else warp_sort_store_s<4>(v, dst, m);
 }
 
 // Shared-memory counters ctr[key] += 1 for every lane with ok, one atomic
@@ -279,25 +293,19 @@ __device__ __forceinline__ int warp_add(int* ctr, int key, bool ok) {
     return old + __popc(peers & lanemask_lt());
 }
 
-// One warp sorts src[0, m) (m <= kWarpSeg) by the low `bits` bits into
-// dst[0, m): a stable LSD sort on 8-bit digits through buf (2 kWarpSeg
-// values) with 256 counters in cnt, all the warp's own shared memory.  A
-// pass ranks each value among the earlier ones of its digit (32 at a
-// time, lanes of one digit in lane order), scans the counts and scatters
-// into the other half of buf; passes whose digit is the same throughout
-// are skipped.
-__device__ void warp_lsd(const unsigned long long* src, unsigned long long* dst, int m, int bits,
-                         unsigned long long* buf, int* cnt) {
+// Stable LSD passes of one warp over cur[0, m) (m <= kWarpSeg) on the 8-bit
+// digits at shift0, shift0 + 8, ... (passes of them), through the other
+// buffer nxt, with 256 counters in cnt; returns the buffer holding the
+// result.  A pass ranks each value among the earlier ones of its digit (32
+// at a time, lanes of one digit in lane order), scans the counts and
+// scatters; passes whose digit is the same throughout are skipped.
+__device__ unsigned long long* warp_lsd_passes(unsigned long long* cur, unsigned long long* nxt, int m, int shift0,
+                                               int passes, int* cnt) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    unsigned long long* cur = buf;
-    unsigned long long* nxt = buf + kWarpSeg;
-    for (int e = lane; e < m; e += 32) cur[e] = src[e];
-    __syncwarp();
     const int rounds = (m + 31) >> 5;
-    const int passes = (bits + 7) >> 3;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
+        const int shift = shift0 + 8 * p;
         for (int d = lane; d < 256; d += 32) cnt[d] = 0;
         __syncwarp();
         int rk[kWarpRounds];
@@ -351,6 +359,61 @@ __device__ void warp_lsd(const unsigned long long* src, unsigned long long* dst,
         unsigned long long* t = cur;
         cur = nxt;
         nxt = t;
+    }
+    return cur;
+}
+
+// Length of the run of values equal to v[e] above bit ib (the Morton code
+// of a composite) that starts at e, or 0 if e does not start one; lengths
+// are counted up to kTieRunMax + 1.  Only the bits above ib are compared,
+// and the tie fix permutes values only inside such runs, so the answer
+// does not depend on fixes of other runs in progress.
+__device__ __forceinline__ int tie_run_at(const unsigned long long* v, int e, int m, int ib) {
+    const unsigned long long key = v[e] >> ib;
+    if (e > 0 && (v[e - 1] >> ib) == key) return 0;
+    int len = 1;
+    while (e + len < m && len <= kTieRunMax && (v[e + len] >> ib) == key) ++len;
+    return len;
+}
+
+// Insertion sort of v[0, len) (one thread; a run of equal Morton codes
+// ordered by the whole composite, that is by caller index).
+__device__ __forceinline__ void sort_run(unsigned long long* v, int len) {
+    for (int i = 1; i < len; ++i) {
+        const unsigned long long x = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > x) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = x;
+    }
+}
+
+// One warp sorts src[0, m) (m <= kWarpSeg) by the low `bits` bits into
+// dst[0, m), in buf (2 kWarpSeg values) with 256 counters in cnt, all the
+// warp's own shared memory.  The composites are (Morton << ib) | caller
+// index: stable LSD passes on the Morton digits only (bits ib and up), then
+// each run of equal Morton codes is put in caller-index order by one lane.
+// A run longer than kTieRunMax (many particles in one fine cell) makes the
+// warp sort the range on all `bits` bits instead.
+__device__ void warp_lsd(const unsigned long long* src, unsigned long long* dst, int m, int bits, int ib,
+                         unsigned long long* buf, int* cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < m; e += 32) buf[e] = src[e];
+    __syncwarp();
+    const int mpasses = bits > ib ? (bits - ib + 7) >> 3 : 0;
+    unsigned long long* cur = warp_lsd_passes(buf, buf + kWarpSeg, m, ib, mpasses, cnt);
+    bool long_run = false;
+    for (int e = lane; e < m; e += 32) long_run = long_run || tie_run_at(cur, e, m, ib) > kTieRunMax;
+    if (__any_sync(kFull, long_run)) {
+        cur = warp_lsd_passes(cur, cur == buf ? buf + kWarpSeg : buf, m, 0, (bits + 7) >> 3, cnt);
+    } else {
+        for (int e = lane; e < m; e += 32) {
+            const int len = tie_run_at(cur, e, m, ib);
+            if (len > 1) sort_run(cur + e, len);
+        }
+        __syncwarp();
     }
     for (int e = lane; e < m; e += 32) dst[e] = cur[e];
 }
@@ -421,7 +484,8 @@ __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, in
 // words holding (flag, particle sum, chunk sum) in (2, 31, 31) bits.
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(
     const int* __restrict__ count, int tc, int C, int* __restrict__ cell_start, int* __restrict__ ccs,
-    int* __restrict__ chunk_cell, long long max_chunks, int* __restrict__ huge, long long huge_cap,
+    int4* __restrict__ chunk_span, const int* __restrict__ vol_cell_base, int n_vol, long long max_chunks,
+    int* __restrict__ huge, long long huge_cap,
     int4* __restrict__ wsegs, long long wseg_cap, int4* __restrict__ bsegs, long long bseg_cap, int sort_bits,
     BinCounters* bc, unsigned long long* status, long long* err, unsigned long long* check) {
     constexpr int kWarps = kScanThreads / 32;
@@ -514,8 +578,10 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(
         ccs[c] = (int)rb;
         if (c == tc) break;
         const int m = cnt[k], nch = (m + C - 1) / C;
+        const int v = nch > 0 && n_vol > 1 ? volume_of_cell((int)c, vol_cell_base, n_vol) : 0;
         for (int j = 0; j < nch; ++j)
-            if (SR_BOUND((long long)rb + j < max_chunks, check, kChkBinScan)) chunk_cell[rb + j] = (int)c;
+            if (SR_BOUND((long long)rb + j < max_chunks, check, kChkBinScan))
+                chunk_span[rb + j] = make_int4((int)c, (int)ra + j * C, min(C, m - j * C), v);
         if (m > kSegTile) {
             const int h = atomicAdd(&bc->n_huge, 1);
             if (SR_BOUND(h < huge_cap, check, kChkBinScan)) huge[h] = (int)c;
@@ -574,11 +640,18 @@ __global__ void __launch_bounds__(kSplitThreads) k_split(unsigned long long* __r
         const int mm = SR_BOUND(base >= 0 && m >= 0 && (long long)base + m <= n, check, kChkBinSort) ? m : 0;
         if (threadIdx.x < 256) hist[threadIdx.x] = 0;
         __syncthreads();
-        for (int e0 = warp * 32; e0 < mm; e0 += kSplitThreads) {
-            const int e = e0 + lane;
-            const bool ok = e < mm;
-            const int d = ok ? (int)((comp[base + e] >> top) & 255ull) : 0;
-            warp_add(hist, d, ok);
+        for (int e0 = warp * 32 * kSplitRounds; e0 < mm; e0 += kSplitThreads * kSplitRounds) {
+            unsigned long long v[kSplitRounds];          // the rounds' loads in flight together
+#pragma unroll
+            for (int r = 0; r < kSplitRounds; ++r) {
+                const int e = e0 + 32 * r + lane;
+                v[r] = e < mm ? comp[base + e] : 0ull;
+            }
+#pragma unroll
+            for (int r = 0; r < kSplitRounds; ++r) {
+                const int e = e0 + 32 * r + lane;
+                warp_add(hist, (int)((v[r] >> top) & 255ull), e < mm);
+            }
         }
         __syncthreads();
         // exclusive scan over the 256 buckets by the first 8 warps
@@ -603,12 +676,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_split(unsigned long long* __r
             fill[threadIdx.x] = before + ex;
         }
         __syncthreads();
-        for (int e0 = warp * 32; e0 < mm; e0 += kSplitThreads) {
-            const int e = e0 + lane;
-            const bool ok = e < mm;
-            const unsigned long long v = ok ? comp[base + e] : 0ull;
-            const int at = warp_add(fill, (int)((v >> top) & 255ull), ok);
-            if (ok) scratch[base + at] = v;
+        for (int e0 = warp * 32 * kSplitRounds; e0 < mm; e0 += kSplitThreads * kSplitRounds) {
+            unsigned long long v[kSplitRounds];
+#pragma unroll
+            for (int r = 0; r < kSplitRounds; ++r) {
+                const int e = e0 + 32 * r + lane;
+                v[r] = e < mm ? comp[base + e] : 0ull;
+            }
+#pragma unroll
+            for (int r = 0; r < kSplitRounds; ++r) {
+                const int e = e0 + 32 * r + lane;
+                const int at = warp_add(fill, (int)((v[r] >> top) & 255ull), e < mm);
+                if (e < mm) scratch[base + at] = v[r];
+            }
         }
         __syncthreads();
         // buckets: one value goes straight back, the rest are listed (a
@@ -688,103 +768,147 @@ __device__ void seg_pass(const unsigned long long* src, unsigned long long* dst,
     }
 }
 
+// Stable LSD passes of the block over cur[0, mm) on the 8-bit digits at
+// shift0, shift0 + 8, ... (passes of them; at most kSegMaxPasses).  In
+// shared memory (in_smem, mm <= kSegTile) each pass goes back into cur;
+// otherwise passes alternate between cur and alt.  Returns the buffer
+// holding the result.  The digit counts of all passes come from one read;
+// passes whose digit is the same for the whole range are skipped.
+__device__ unsigned long long* block_lsd_passes(unsigned long long* cur, unsigned long long* alt, int mm, int shift0,
+                                                int passes, bool in_smem, int (*hist)[256], int* run,
+                                                int (*wh)[256], int* warp_tot, unsigned long long* check) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < kSegMaxPasses * 256; i += kSegThreads) (&hist[0][0])[i] = 0;
+    __syncthreads();
+    for (int e0 = warp * 32; e0 < mm; e0 += kSegThreads) {
+        const int e = e0 + lane;
+        const bool in = e < mm;
+        const unsigned long long v = in ? cur[e] : 0ull;
+        for (int p = 0; p < passes; ++p) warp_add(hist[p], (int)((v >> (shift0 + 8 * p)) & 255ull), in);
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        const int h = hist[p][threadIdx.x];
+        if (__syncthreads_or(h == mm)) continue;             // one digit throughout: order kept
+        run[threadIdx.x] = block_exclusive_scan256(h, warp_tot);
+        __syncthreads();
+        unsigned long long* dst = in_smem ? cur : alt;
+        seg_pass(cur, dst, mm, shift0 + 8 * p, run, wh, check);
+        if (!in_smem) {
+            alt = cur;
+            cur = dst;
+        }
+    }
+    return cur;
+}
+
 // The listed ranges, sorted by the low `bits` bits into the composites
-// array (from it, or from scratch where the split left a bucket).  First
-// the warp list, one warp per range (dealt round robin): bitonic in registers up
-// to kSmallCell, else warp_lsd in the warp's part of shared memory.  Then
-// the block list, one block per range: a stable LSD sort on 8-bit digits,
-// in shared memory up to kSegTile values, else through the composites and
-// scratch arrays in turn; passes whose digit is the same for the whole
-// range are skipped.
-__global__ void __launch_bounds__(kSegThreads) k_sort_segments(unsigned long long* __restrict__ comp,
+// array (from it, or from scratch where the split left a bucket).  PHASE 0,
+// the warp list, one warp per range (dealt round robin): bitonic in
+// registers up to kSmallCell, else warp_lsd in the warp's part of shared
+// memory.  PHASE 1, the block list, one block per range: stable LSD passes
+// on the Morton digits, in shared memory up to kSegTile values, else
+// through the composites and scratch arrays in turn, then the runs of
+// equal Morton codes in caller-index order (all bits for a range with a
+// run longer than kTieRunMax); passes whose digit is the same for the
+// whole range are skipped.
+template <int PHASE>   // 0: the warp list, 1: the block list
+__global__ void __launch_bounds__(kSegThreads, 3) k_sort_segments(unsigned long long* __restrict__ comp,
                                                                unsigned long long* __restrict__ scratch,
                                                                const int4* __restrict__ wsegs,
                                                                const int4* __restrict__ bsegs, BinCounters* bc,
-                                                               int n, unsigned long long* check) {
+                                                               int n, int ib, unsigned long long* check) {
     extern __shared__ unsigned long long sv[];   // see kSortSmem
     int (*hist)[256] = reinterpret_cast<int (*)[256]>(sv + kSegTile);   // block phase only
     __shared__ int wh[kSegWarps][256];
     __shared__ int run[256];
     __shared__ int warp_tot[8];
     __shared__ int s_item;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // warp list: items dealt round robin to the grid's warps, the next
-    // item's entry loaded while the current one is sorted
-    const int n_w = bc->n_wseg, stride = gridDim.x * kSegWarps;
+    const int warp = threadIdx.x >> 5;
+    // warp list: items dealt round robin to the grid's warps; the entry two
+    // items ahead and the values of the next small range are loaded while
+    // the current range is sorted
+    const int n_w = PHASE == 0 ? bc->n_wseg : 0, stride = gridDim.x * kSegWarps;
+    auto entry = [&](int i) {
+        int4 g = i < n_w ? wsegs[i] : make_int4(0, 0, 0, 0);
+        if (!SR_BOUND(g.x >= 0 && g.y >= 0 && g.y <= kWarpSeg && (long long)g.x + g.y <= n && g.w >= 0 && g.w <= 64,
+                      check, kChkBinSort))
+            g = make_int4(0, 0, 0, 0);
+        return g;
+    };
     int item = blockIdx.x * kSegWarps + warp;
-    int4 sg = item < n_w ? wsegs[item] : make_int4(0, 0, 0, 0);
+    int4 sg = entry(item), sn = entry(item + stride);
+    unsigned long long pv[4];
+    load_small((sg.z ? scratch : comp) + sg.x, sg.y, pv);
     while (item < n_w) {
-        const int next = item + stride;
-        const int4 sn = next < n_w ? wsegs[next] : make_int4(0, 0, 0, 0);
-        if (SR_BOUND(sg.x >= 0 && sg.y >= 0 && sg.y <= kWarpSeg && (long long)sg.x + sg.y <= n && sg.w >= 0 &&
-                         sg.w <= 64,
-                     check, kChkBinSort)) {
-            const unsigned long long* src = (sg.z ? scratch : comp) + sg.x;
-            if (sg.y <= kSmallCell) warp_sort_small(src, comp + sg.x, sg.y);
-            else warp_lsd(src, comp + sg.x, sg.y, sg.w, sv + 2 * warp * kWarpSeg, wh[warp]);
-        }
-        item = next;
+        const int4 sn2 = entry(item + 2 * stride);
+        unsigned long long nv[4];
+        load_small((sn.z ? scratch : comp) + sn.x, sn.y, nv);
+        if (sg.y <= kSmallCell) warp_sort_store(pv, comp + sg.x, sg.y);
+        else warp_lsd((sg.z ? scratch : comp) + sg.x, comp + sg.x, sg.y, sg.w, ib, sv + 2 * warp * kWarpSeg, wh[warp]);
+        item += stride;
         sg = sn;
+        sn = sn2;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) pv[t] = nv[t];
     }
-    __syncthreads();
-    while (true) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&bc->next_bseg, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= bc->n_bseg) break;
-        const int4 sg = bsegs[item];
-        const int off = sg.x, m = sg.y, bits = sg.w;
-        const bool ok = SR_BOUND(off >= 0 && m >= 0 && (long long)off + m <= n && bits >= 0 && bits <= 64,
-                                 check, kChkBinSort);
-        const int passes = ok ? (bits + 7) / 8 : 0;
-        const int mm = ok ? m : 0;
-        unsigned long long* home = comp + off;
-        const unsigned long long* src = (sg.z ? scratch : comp) + off;
-        for (int i = threadIdx.x; i < kSegMaxPasses * 256; i += kSegThreads) (&hist[0][0])[i] = 0;
-        __syncthreads();
-        for (int e0 = warp * 32; e0 < mm; e0 += kSegThreads) {
-            const int e = e0 + lane;
-            const bool in = e < mm;
-            const unsigned long long v = in ? src[e] : 0ull;
-            for (int p = 0; p < passes; ++p) warp_add(hist[p], (int)((v >> (8 * p)) & 255ull), in);
-        }
-        __syncthreads();
-        const bool in_smem = mm <= kSegTile;
-        unsigned long long* cur = in_smem ? sv : const_cast<unsigned long long*>(src);
-        unsigned long long* nxt = in_smem ? sv : (sg.z ? comp : scratch) + off;
-        if (in_smem)
-            for (int e = threadIdx.x; e < mm; e += kSegThreads) sv[e] = src[e];
-        __syncthreads();
-        for (int p = 0; p < passes; ++p) {
-            const int h = hist[p][threadIdx.x];
-            if (__syncthreads_or(h == mm)) continue;             // one digit throughout: order kept
-            run[threadIdx.x] = block_exclusive_scan256(h, warp_tot);
+    if constexpr (PHASE == 1) {
+        while (true) {
+            // from the end of the list: the huge cells' buckets (appended
+            // by k_split after the cell scan's ranges), the largest ranges,
+            // start first
+            if (threadIdx.x == 0) s_item = atomicAdd(&bc->next_bseg, 1);
             __syncthreads();
-            seg_pass(cur, nxt, mm, 8 * p, run, wh, check);
-            if (!in_smem) {
-                unsigned long long* t = cur;
-                cur = nxt;
-                nxt = t;
+            const int taken = s_item;
+            if (taken >= bc->n_bseg) break;
+            const int4 sg = bsegs[bc->n_bseg - 1 - taken];
+            const int off = sg.x, m = sg.y, bits = sg.w;
+            const bool ok = SR_BOUND(off >= 0 && m >= 0 && (long long)off + m <= n && bits >= 0 && bits <= 64,
+                                     check, kChkBinSort);
+            const int mm = ok ? m : 0;
+            unsigned long long* home = comp + off;
+            unsigned long long* src = (sg.z ? scratch : comp) + off;
+            const bool in_smem = mm <= kSegTile;
+            unsigned long long* cur = in_smem ? sv : src;
+            unsigned long long* alt = in_smem ? sv : (sg.z ? comp : scratch) + off;
+            if (in_smem)
+                for (int e = threadIdx.x; e < mm; e += kSegThreads) sv[e] = src[e];
+            __syncthreads();
+            // Morton digits first (stable), then runs of equal Morton codes in
+            // caller-index order, as warp_lsd; a long run: all bits instead
+            const int mpasses = bits > ib ? (bits - ib + 7) / 8 : 0;
+            cur = block_lsd_passes(cur, alt, mm, ib, mpasses, in_smem, hist, run, wh, warp_tot, check);
+            alt = in_smem ? sv : (cur == src ? (sg.z ? comp : scratch) + off : src);
+            bool long_run = false;
+            for (int e = threadIdx.x; e < mm; e += kSegThreads)
+                long_run = long_run || tie_run_at(cur, e, mm, ib) > kTieRunMax;
+            if (__syncthreads_or(long_run)) {
+                cur = block_lsd_passes(cur, alt, mm, 0, (bits + 7) / 8, in_smem, hist, run, wh, warp_tot, check);
+            } else {
+                for (int e = threadIdx.x; e < mm; e += kSegThreads) {
+                    const int len = tie_run_at(cur, e, mm, ib);
+                    if (len > 1) sort_run(cur + e, len);
+                }
+                __syncthreads();
             }
+            if (ok && cur != home)
+                for (int e = threadIdx.x; e < mm; e += kSegThreads) home[e] = cur[e];
+            __syncthreads();
         }
-        if (ok && cur != home)
-            for (int e = threadIdx.x; e < mm; e += kSegThreads) home[e] = cur[e];
-        __syncthreads();
     }
 }
 
 // One chunk: slot offsets, indices and flags, anchor, bounding box and
-// counts from the caller indices of its slots (lane l holds slots l + 32 s).
+// counts from the caller indices of its slots and their positions (lane l
+// holds slots l + 32 s; x3 already loaded).
 template <int K>
 __device__ __forceinline__ void fill_chunk(
-    long long k, int cell, const int (&idx_in)[K], const bool (&valid_in)[K], int cnt,
-    const double* __restrict__ pos, const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base,
-    int n_vol, float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
-    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, const unsigned char* __restrict__ active, int n,
-    unsigned long long* check) {
+    long long k, int v, const int (&idx_in)[K], const bool (&valid_in)[K], const double (&x3)[K][3], int cnt,
+    const VolDev* __restrict__ vols, float4* __restrict__ slot_pos, int* __restrict__ slot_idx,
+    int4* __restrict__ chunk_meta, float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi,
+    const unsigned char* __restrict__ active) {
     constexpr int C = 32 * K;
     const int lane = threadIdx.x & 31;
-    const int v = n_vol > 1 ? volume_of_cell(cell, vol_cell_base, n_vol) : 0;
     const VolDev& V = vols[v];
     int orig[K], q[K][3], F[K][3];
     unsigned long long mant[K][3];
@@ -795,27 +919,24 @@ __device__ __forceinline__ void fill_chunk(
     for (int s = 0; s < K; ++s) {
         valid[s] = valid_in[s];
         fast[s] = false;
-        orig[s] = -1;
+        orig[s] = valid[s] ? idx_in[s] : -1;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) { q[s][ax] = 0; t[s][ax] = 0.0; F[s][ax] = -1; mant[s][ax] = 0ull; }
         if (valid[s]) {
-            orig[s] = idx_in[s];
-            if (!SR_BOUND(orig[s] >= 0 && orig[s] < n, check, kChkChunkFill)) orig[s] = 0;
-            const double x3[3] = {pos[3ll * orig[s]], pos[3ll * orig[s] + 1], pos[3ll * orig[s] + 2]};
             // the integer path needs t >= 1 on every axis for the offsets;
             // q holds the unclamped floor(t) there (the anchor is clamped)
             bool f = true;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax)
-                f = f && (V.h_pow2 ? fine_axis_bits(x3[ax], ubox, V.inv_h_exp, q[s][ax], mant[s][ax], F[s][ax])
-                                   : fine_axis_quot(x3[ax], ubox, V.h, V.inv_h, q[s][ax], mant[s][ax],
+                f = f && (V.h_pow2 ? fine_axis_bits(x3[s][ax], ubox, V.inv_h_exp, q[s][ax], mant[s][ax], F[s][ax])
+                                   : fine_axis_quot(x3[s][ax], ubox, V.h, V.inv_h, q[s][ax], mant[s][ax],
                                                     F[s][ax])) &&
                     F[s][ax] >= 0;
             fast[s] = f;
             if (!f) {
                 bool bad = false;
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) fine_axis(x3[ax], V, t[s][ax], q[s][ax], bad);
+                for (int ax = 0; ax < 3; ++ax) fine_axis(x3[s][ax], V, t[s][ax], q[s][ax], bad);
             }
         }
     }
@@ -863,43 +984,66 @@ __device__ __forceinline__ void fill_chunk(
     }
 }
 
-// One warp per chunk: the caller indices of its slots from the sorted
-// composites, then the chunk's slots and records; perm[sorted position] =
-// caller index.
-template <int K>
-__global__ void __launch_bounds__(256) k_chunk_fill(
+// One warp per group of U consecutive chunks: the caller indices of their
+// slots from the sorted composites, then the chunks' slots and records;
+// perm[sorted position] = caller index.  Each chunk's record (cell, first
+// sorted row, count, volume) comes from the cell scan, so a chunk costs two
+// dependent loads (composites, then positions); the U chunks' loads are
+// issued together to keep more of them in flight.
+template <int K, int U>
+__global__ void __launch_bounds__(256, 3) k_chunk_fill(
     const double* __restrict__ pos, const unsigned long long* __restrict__ comp, int ib,
-    const int* __restrict__ cell_start, const int* __restrict__ ccs, const int* __restrict__ chunk_cell,
-    int total_cells, const VolDev* __restrict__ vols, const int* __restrict__ vol_cell_base, int n_vol,
-    float4* __restrict__ slot_pos, int* __restrict__ slot_idx, int4* __restrict__ chunk_meta,
-    float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi, int* __restrict__ perm,
-    const unsigned char* __restrict__ active, int n, long long max_chunks, unsigned long long* check) {
-    constexpr int C = 32 * K;
+    const int4* __restrict__ chunk_span, const int* __restrict__ ccs, int total_cells,
+    const VolDev* __restrict__ vols, int n_vol, float4* __restrict__ slot_pos, int* __restrict__ slot_idx,
+    int4* __restrict__ chunk_meta, float4* __restrict__ chunk_lo, float4* __restrict__ chunk_hi,
+    int* __restrict__ perm, const unsigned char* __restrict__ active, int n, long long max_chunks,
+    unsigned long long* check) {
+    [[maybe_unused]] constexpr int C = 32 * K;     // bounds checks only
     const int lane = threadIdx.x & 31;
     const int n_chunks = ccs[total_cells];
     const int warps = gridDim.x * (blockDim.x >> 5);
     const unsigned long long imask = (1ull << ib) - 1ull;
-    for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n_chunks; k += warps) {
-        const int cell = chunk_cell[k];
-        if (!SR_BOUND(k < max_chunks && cell >= 0 && cell < total_cells, check, kChkChunkFill)) continue;
-        const int base = cell_start[cell];
-        const int m = max(0, cell_start[cell + 1] - base);
-        const int kc = k - ccs[cell];
-        if (!SR_BOUND(base >= 0 && (long long)base + m <= n && kc >= 0, check, kChkChunkFill)) continue;
-        int idx[K];
-        bool valid[K];
+    for (int k0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * U; k0 < n_chunks; k0 += warps * U) {
+        int4 sp[U];
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            const int e = kc * C + lane + 32 * s;
-            valid[s] = e < m;
-            idx[s] = -1;
-            if (valid[s]) {
-                idx[s] = (int)(comp[base + e] & imask);
-                perm[base + e] = idx[s];
-            }
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u;
+            sp[u] = make_int4(-1, 0, 0, 0);
+            if (k < n_chunks && SR_BOUND(k < max_chunks, check, kChkChunkFill)) sp[u] = chunk_span[k];
+            if (!SR_BOUND(sp[u].x < 0 || (sp[u].y >= 0 && sp[u].z > 0 && sp[u].z <= C &&
+                                          (long long)sp[u].y + sp[u].z <= n && sp[u].w >= 0 && sp[u].w < n_vol),
+                          check, kChkChunkFill))
+                sp[u].x = -1;
         }
-        fill_chunk<K>(k, cell, idx, valid, min(C, m - kc * C), pos, vols, vol_cell_base, n_vol, slot_pos, slot_idx,
-                      chunk_meta, chunk_lo, chunk_hi, active, n, check);
+        int idx[U][K];
+        bool valid[U][K];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                const int e = lane + 32 * s;
+                valid[u][s] = sp[u].x >= 0 && e < sp[u].z;
+                idx[u][s] = valid[u][s] ? (int)(comp[sp[u].y + e] & imask) : -1;
+            }
+        double x3[U][K][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int s = 0; s < K; ++s) {
+                if (valid[u][s] && !SR_BOUND(idx[u][s] >= 0 && idx[u][s] < n, check, kChkChunkFill)) idx[u][s] = 0;
+                const long long o = valid[u][s] ? 3ll * idx[u][s] : 0ll;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) x3[u][s][ax] = valid[u][s] ? pos[o + ax] : 0.0;
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (sp[u].x < 0) continue;                   // warp-uniform
+#pragma unroll
+            for (int s = 0; s < K; ++s)
+                if (valid[u][s]) perm[sp[u].y + lane + 32 * s] = idx[u][s];
+            fill_chunk<K>(k0 + u, sp[u].w, idx[u], valid[u], x3[u], sp[u].z, vols, slot_pos, slot_idx, chunk_meta,
+                          chunk_lo, chunk_hi, active);
+        }
     }
 }
 
@@ -921,7 +1065,17 @@ int bin_alloc(sr_plan* p) {
     if (e == cudaSuccess) e = cudaMalloc(&B.wsegs, sizeof(int4) * (size_t)B.wseg_cap);
     if (e == cudaSuccess) e = cudaMalloc(&B.bsegs, sizeof(int4) * (size_t)B.bseg_cap);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sort_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+        e = cudaFuncSetAttribute(k_sort_segments<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sort_segments<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem);
+    // one wave of resident blocks: every warp starts its share of the
+    // round-robin warp list at once (a second wave would start late)
+    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, ph == 0 ? k_sort_segments<0> : k_sort_segments<1>, kSegThreads, kSortSmem);
+        B.seg_blocks[ph] = (per_sm > 0 ? per_sm : 1) * p->sm_count;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "bin_alloc");
     char* r = static_cast<char*>(B.region);
     B.counters = reinterpret_cast<BinCounters*>(r);
@@ -956,7 +1110,8 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, cons
         SR_LAUNCH_CHECK("k_keys");
     }
     const int tiles = (tc + 1 + kCellTile - 1) / kCellTile;
-    k_cell_scan<<<tiles, kScanThreads, 0, st>>>(B.count, tc, C, p->cell_start, p->ccs, p->chunk_cell, p->max_chunks,
+    k_cell_scan<<<tiles, kScanThreads, 0, st>>>(B.count, tc, C, p->cell_start, p->ccs, p->chunk_span, p->vol_cell_base,
+                                                p->n_vol, p->max_chunks,
                                                 B.huge, B.huge_cap, B.wsegs, B.wseg_cap, B.bsegs, B.bseg_cap, bits,
                                                 B.counters, B.status,
                                                 &p->ctr->err, check);
@@ -968,23 +1123,27 @@ int launch_bin(sr_plan* p, const double* pos, long long n, cudaStream_t st, cons
         k_split<<<p->sm_count, kSplitThreads, 0, st>>>(p->keys[1], p->keys[0], p->cell_start, B.huge, B.counters,
                                                        B.wsegs, B.wseg_cap, B.bsegs, B.bseg_cap, bits, ni, check);
         SR_LAUNCH_CHECK("k_split");
-        k_sort_segments<<<p->sm_count * 4, kSegThreads, kSortSmem, st>>>(p->keys[1], p->keys[0], B.wsegs, B.bsegs,
-                                                                          B.counters, ni, check);
-        SR_LAUNCH_CHECK("k_sort_segments");
+        k_sort_segments<0><<<B.seg_blocks[0], kSegThreads, kSortSmem, st>>>(p->keys[1], p->keys[0], B.wsegs,
+                                                                             B.bsegs, B.counters, ni, ib, check);
+        SR_LAUNCH_CHECK("k_sort_segments<warp>");
+        k_sort_segments<1><<<B.seg_blocks[1], kSegThreads, kSortSmem, st>>>(p->keys[1], p->keys[0], B.wsegs,
+                                                                             B.bsegs, B.counters, ni, ib, check);
+        SR_LAUNCH_CHECK("k_sort_segments<block>");
     }
-    long long want = (p->max_chunks + 7) / 8;
+    const int U = p->chunk_k == 2 ? kFillU2 : kFillU1;
+    long long want = (p->max_chunks + 8 * U - 1) / (8 * U);
     long long cap = (long long)p->sm_count * 16;
     const int blocks = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     if (p->chunk_k == 2)
-        k_chunk_fill<2><<<blocks, 256, 0, st>>>(pos, p->keys[1], ib, p->cell_start, p->ccs, p->chunk_cell, tc, p->vols,
-                                                p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx, p->chunk_meta,
-                                                p->chunk_lo, p->chunk_hi, p->vals[1], active, ni, p->max_chunks,
-                                                check);
+        k_chunk_fill<2, kFillU2><<<blocks, 256, 0, st>>>(pos, p->keys[1], ib, p->chunk_span, p->ccs, tc, p->vols,
+                                                         p->n_vol, p->slot_pos, p->slot_idx, p->chunk_meta,
+                                                         p->chunk_lo, p->chunk_hi, p->vals[1], active, ni,
+                                                         p->max_chunks, check);
     else
-        k_chunk_fill<1><<<blocks, 256, 0, st>>>(pos, p->keys[1], ib, p->cell_start, p->ccs, p->chunk_cell, tc, p->vols,
-                                                p->vol_cell_base, p->n_vol, p->slot_pos, p->slot_idx, p->chunk_meta,
-                                                p->chunk_lo, p->chunk_hi, p->vals[1], active, ni, p->max_chunks,
-                                                check);
+        k_chunk_fill<1, kFillU1><<<blocks, 256, 0, st>>>(pos, p->keys[1], ib, p->chunk_span, p->ccs, tc, p->vols,
+                                                         p->n_vol, p->slot_pos, p->slot_idx, p->chunk_meta,
+                                                         p->chunk_lo, p->chunk_hi, p->vals[1], active, ni,
+                                                         p->max_chunks, check);
     SR_LAUNCH_CHECK("k_chunk_fill");
     p->sorted = 1;
     return launch_cost_and_order(p, st);

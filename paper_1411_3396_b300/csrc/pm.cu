@@ -162,7 +162,7 @@ __device__ __forceinline__ void tile_add(unsigned* lo, unsigned* hi, unsigned lo
 
 __global__ void __launch_bounds__(kDepWarps * 32)
 k_cic_deposit_chunks(const double* __restrict__ pos, const int* __restrict__ ccs, int total_cells,
-                     const int* __restrict__ chunk_cell, const int* __restrict__ slot_idx, int chunk, int n_c,
+                     const int4* __restrict__ chunk_span, const int* __restrict__ slot_idx, int chunk, int n_c,
                      double ratio, int wt, double box, double inv_d, int inv_s, int n, float scale,
                      unsigned long long* __restrict__ grid) {
     __shared__ unsigned tlo[kDepWarps][kDepTileMax], thi[kDepWarps][kDepTileMax];
@@ -173,7 +173,7 @@ k_cic_deposit_chunks(const double* __restrict__ pos, const int* __restrict__ ccs
     const int tsize = wt * wt * wt;
     const int warps = gridDim.x * kDepWarps;
     for (int k = blockIdx.x * kDepWarps + (threadIdx.x >> 5); k < n_chunks; k += warps) {
-        const int cell = chunk_cell[k];
+        const int cell = chunk_span[k].x;
         const int cx = cell % n_c, cy = (cell / n_c) % n_c, cz = cell / (n_c * n_c);
         const int x0 = (int)floor(cx * ratio), y0 = (int)floor(cy * ratio), z0 = (int)floor(cz * ratio);
         for (int i = lane; i < tsize; i += 32) lo[i] = hi[i] = 0u;
@@ -851,7 +851,7 @@ int sr_pm_deposit_binned(sr_pm* pm, const sr_plan* plan, const double* pos, int6
     const long long want = (plan->max_chunks + kDepWarps - 1) / kDepWarps;
     const int blocks = (int)std::max(1LL, std::min(want, 8LL * sms));
     k_cic_deposit_chunks<<<blocks, kDepWarps * 32, 0, st>>>(
-        pos, plan->ccs, (int)plan->total_cells, plan->chunk_cell, plan->slot_idx, 32 * plan->chunk_k, n_c, ratio,
+        pos, plan->ccs, (int)plan->total_cells, plan->chunk_span, plan->slot_idx, 32 * plan->chunk_k, n_c, ratio,
         wt, pm->box, pm->n / pm->box, mesh_exp(pm), pm->n, (float)scale, pm->fx);
     SR_LAUNCH_CHECK("k_cic_deposit_chunks");
     pm->last_np = n;

@@ -203,6 +203,7 @@ struct BinScratch {
     long long wseg_cap = 0;
     int4* bsegs = nullptr;                // ranges to sort by block, same fields
     long long bseg_cap = 0;
+    int seg_blocks[2] = {0, 0};           // resident blocks of the two segment-sort phases
 };
 
 struct ScanScratch {
@@ -243,7 +244,7 @@ struct sr_plan {
     int sorted = 0;                        // buffer index holding the sorted result
     int* cell_start = nullptr;             // total_cells + 1
     int* ccs = nullptr;                    // cell -> first chunk, total_cells + 1
-    int* chunk_cell = nullptr;             // chunk -> cell
+    int4* chunk_span = nullptr;            // chunk -> cell, first sorted row, particle count, volume
     int4* chunk_meta = nullptr;            // anchor qx, qy, qz, volume
     float4* chunk_lo = nullptr;            // bbox min, w = count (int bits)
     float4* chunk_hi = nullptr;

@@ -183,6 +183,43 @@ def test_bin_dense_cells_every_sort_path(chunk):
         assert a.tobytes() == to_np(plan.export(k)).tobytes()
 
 
+@pytest.mark.parametrize("chunk", [32, 64])
+def test_bin_tie_runs_each_sort_path(chunk):
+    # cells sorted by a warp (129..512 particles) or a block (513..2048 in
+    # shared memory, larger ones split and their buckets sorted) order the
+    # Morton code first and then each run of equal codes by caller index;
+    # a run longer than 32 makes them sort the range on every bit instead.
+    # Runs of 2..32 and of 33 and 40 in each path, in distinct cells
+    L, n_c = 32.0, 8
+    side = L / n_c
+    cells = [                           # (particles, extent of the cube that holds them, runs)
+        (300, 3.6, [2, 3, 17, 32]),     # warp LSD, runs fixed in place
+        (300, 3.6, [2, 33]),            # warp LSD, a run over the limit
+        (1500, 3.6, [2, 5, 32, 32]),    # block sort in shared memory
+        (1500, 3.6, [40]),              # the same, over the limit
+        (6000, 0.8, [2, 9, 31, 32]),    # split: four buckets of about 1500, block sort
+        # split: one bucket of 6000 (a 0.5 x 0.5 x 1 box of 1024 fine cells)
+        # sorted through global memory, with and without a run over the limit
+        (6000, [0.85, 0.35, 0.35], [2, 32]),
+        (6000, [0.85, 0.35, 0.35], [33, 3]),
+    ]
+    parts = []
+    for k, (m, ext, runs) in enumerate(cells):
+        corner = np.array([k * side, 2 * side, 0.0])
+        rng = np.random.default_rng(60 + k)
+        parts.append(corner + 0.1 + rng.random((m - sum(runs), 3)) * ext)
+        # each run: coincident particles alone in a fine cell (y, z below
+        # the cloud's 0.1; the first row of fine cells), distinct along x
+        for j, r in enumerate(runs):
+            parts.append(np.tile(corner + [0.11 + 0.1 * j, 0.02, 0.02], (r, 1)))
+    pos = np.concatenate(parts)
+    pos = pos[np.random.default_rng(77).permutation(len(pos))]
+    vols = [(pos, L)]
+    plan = _run_bin(vols, dict(rc=3.0, eps=0.1, sigma=0.8), n_cells=[n_c], chunk_size=chunk)
+    _compare(plan, vols)
+    plan.status()
+
+
 @pytest.mark.parametrize("sub_bits,chunk", [(6, 32), (3, 64), (6, 64)])
 def test_bin_power_of_two_side_with_sub_cells(sub_bits, chunk):
     # box 32, 8 cells: h = 4 / 2^b is a power of two (the integer path of the
