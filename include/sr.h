@@ -359,6 +359,34 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
                  int64_t n, void* stream);
 
 /*
+ * sr_step_host_submit / sr_step_host_wait -- the step of sr_step_host for a
+ * stream of independent inputs (one short-range step of Sec. 2.1 per
+ * input), pipelined: submit enqueues the step and returns without waiting,
+ * so the uploads of one step run while the step before it computes, and
+ * its read-back while the next one computes.
+ *   submit: copy pos (host binary64 rows) and vel (host float4 rows) to one
+ *           of two plan-owned staging sets (used in turn) on a plan-owned
+ *           upload stream; sr_bin and sr_force_kick on `stream` once those
+ *           copies are done; copy the updated vel and, if acc is not null,
+ *           the accelerations (host float4 rows) back on a plan-owned
+ *           download stream.  Steps run on `stream` in submission order
+ *           (they share the plan's workspace).  The results are the same
+ *           bits as sr_step_host's for the same inputs.
+ *   wait:   blocks until every submitted step's read-back is done.
+ * The host buffers of a step must stay valid and unchanged until its
+ * read-back is done (sr_step_host_wait, or two submits later, when its
+ * staging set is reused); pos is read, vel is read and then overwritten.
+ * Page-locked host buffers are needed for the copies to overlap.  The first
+ * submit allocates the two staging sets (2 x 56 bytes per particle of the
+ * plan's capacity), two streams and six events.  Errors: SR_ERR_ARG (null
+ * plan or buffer), SR_ERR_CAPACITY (n above the capacity), those of sr_bin
+ * and sr_force_kick, SR_ERR_CUDA.
+ */
+int sr_step_host_submit(sr_plan* plan, const double* pos, float* vel, float* acc, float dt,
+                        int64_t n, void* stream);
+int sr_step_host_wait(sr_plan* plan);
+
+/*
  * sr_plan_set_variant -- select the pair-kernel variant used by sr_force
  * (same arithmetic and summation order, different launch shape):
  *   0..3: 256-thread blocks, at least 1, 2, 3, 4 resident per SM

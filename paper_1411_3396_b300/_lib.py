@@ -76,6 +76,8 @@ SIGNATURES = {
     "sr_plan_status": (c_int, [c_void_p, c_void_p]),
     "sr_plan_copy": (c_int, [c_void_p, c_int, c_void_p, c_int64, c_void_p]),
     "sr_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
+    "sr_step_host_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int64, c_void_p]),
+    "sr_step_host_wait": (c_int, [c_void_p]),
     "sr_plan_set_variant": (c_int, [c_void_p, c_int]),
     "sr_autotune": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_float), c_void_p]),
     "sr_bin_active": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),

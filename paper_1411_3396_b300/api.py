@@ -296,6 +296,23 @@ class Plan:
         self.n = n
         self.binnings += 1
 
+    def step_host_submit(self, pos, vel, acc, dt: float):
+        """step_host for a stream of independent inputs, without waiting:
+        the uploads of this step overlap the step before it, its read-back
+        the step after it.  pos, vel and acc (or None) are page-locked CPU
+        tensors that must stay untouched until step_host_wait() returns (or
+        two submits later); vel is overwritten with the kicked velocities."""
+        n = pos.shape[0]
+        check(load().sr_step_host_submit(self._h, c_void_p(pos.data_ptr()), c_void_p(vel.data_ptr()),
+                                         c_void_p(acc.data_ptr()) if acc is not None else c_void_p(0),
+                                         float(dt), n, _stream()))
+        self.n = n
+        self.binnings += 1
+
+    def step_host_wait(self):
+        """Block until every submitted step's results are in host memory."""
+        check(load().sr_step_host_wait(self._h))
+
     def _need_binned(self) -> int:
         if self.n is None:
             raise RuntimeError("bin() must be called first")

@@ -58,6 +58,16 @@ void free_plan(sr_plan* p) {
     if (p->h_side) cudaStreamDestroy(p->h_side);
     if (p->h_fork) cudaEventDestroy(p->h_fork);
     if (p->h_join) cudaEventDestroy(p->h_join);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(p->q_pos[k]);
+        cudaFree(p->q_vel[k]);
+        cudaFree(p->q_acc[k]);
+        if (p->q_loaded[k]) cudaEventDestroy(p->q_loaded[k]);
+        if (p->q_computed[k]) cudaEventDestroy(p->q_computed[k]);
+        if (p->q_freed[k]) cudaEventDestroy(p->q_freed[k]);
+    }
+    if (p->q_up) cudaStreamDestroy(p->q_up);
+    if (p->q_down) cudaStreamDestroy(p->q_down);
     radix_free(p->rs_chunks);
     bin_free(p);
     delete p;
@@ -518,6 +528,52 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
     SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->h_vel_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
     if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
     SR_CUDA_CHECK(cudaStreamSynchronize(st));
+    return SR_OK;
+}
+
+int sr_step_host_submit(sr_plan* p, const double* pos, float* vel, float* acc, float dt, int64_t n, void* stream) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!pos || !vel) return set_error(SR_ERR_ARG, "null host buffer");
+    if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
+    cudaStream_t st = as_stream(stream);
+    int rc;
+    if (!p->q_up) {
+        for (int k = 0; k < 2; ++k) {
+            if ((rc = dalloc(&p->q_pos[k], (size_t)p->capacity * 3)) || (rc = dalloc(&p->q_vel[k], (size_t)p->capacity * 4)) ||
+                (rc = dalloc(&p->q_acc[k], (size_t)p->capacity * 4)))
+                return rc;
+            SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_loaded[k], cudaEventDisableTiming));
+            SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_computed[k], cudaEventDisableTiming));
+            SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_freed[k], cudaEventDisableTiming));
+        }
+        SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->q_down, cudaStreamNonBlocking));
+        SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->q_up, cudaStreamNonBlocking));
+    }
+    const int s = p->q_next;
+    // uploads into set s once the step that used it last has been read back
+    if (p->q_used[s]) SR_CUDA_CHECK(cudaStreamWaitEvent(p->q_up, p->q_freed[s], 0));
+    SR_CUDA_CHECK(cudaMemcpyAsync(p->q_pos[s], pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, p->q_up));
+    SR_CUDA_CHECK(cudaMemcpyAsync(p->q_vel[s], vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, p->q_up));
+    SR_CUDA_CHECK(cudaEventRecord(p->q_loaded[s], p->q_up));
+    // binning and force on the caller's stream, after the step before (the
+    // plan's workspace) and after this set's uploads
+    SR_CUDA_CHECK(cudaStreamWaitEvent(st, p->q_loaded[s], 0));
+    if ((rc = sr_bin(p, p->q_pos[s], n, stream))) return rc;
+    if ((rc = launch_force(p, p->q_acc[s], nullptr, nullptr, st, p->q_vel[s], dt))) return rc;
+    SR_CUDA_CHECK(cudaEventRecord(p->q_computed[s], st));
+    SR_CUDA_CHECK(cudaStreamWaitEvent(p->q_down, p->q_computed[s], 0));
+    SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->q_vel[s], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, p->q_down));
+    if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->q_acc[s], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, p->q_down));
+    SR_CUDA_CHECK(cudaEventRecord(p->q_freed[s], p->q_down));
+    p->q_used[s] = true;
+    p->q_next = 1 - s;
+    return SR_OK;
+}
+
+int sr_step_host_wait(sr_plan* p) {
+    if (!p) return set_error(SR_ERR_ARG, "plan is null");
+    if (!p->q_down) return SR_OK;                    // nothing submitted
+    SR_CUDA_CHECK(cudaStreamSynchronize(p->q_down));
     return SR_OK;
 }
 

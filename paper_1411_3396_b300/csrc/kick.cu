@@ -64,6 +64,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 }
 
 constexpr int kInvFold = 8;        // rows a thread sums in binary32 pairs before each binary64 add
+constexpr int kInvRows = 4;        // rows whose loads a thread issues together
 
 // Block partial sums of the seven invariants.  B300 runs binary64 at a small
 // fraction of its binary32 rate, and a binary64 add per term bound this
@@ -74,7 +75,7 @@ constexpr int kInvFold = 8;        // rows a thread sums in binary32 pairs befor
 // of the fold's terms (an emulation of the scheme on 200 random sets of
 // mixed magnitudes stayed within 1.1e-15 of the sum of the terms'
 // magnitudes of the exact sum).
-__global__ void __launch_bounds__(256) k_inv_partial(long long n, const float4* __restrict__ vel,
+__global__ void __launch_bounds__(256, 4) k_inv_partial(long long n, const float4* __restrict__ vel,
                                                      const float4* __restrict__ acc,
                                                      double* __restrict__ partials) {
     __shared__ double sh[7][256];
@@ -83,34 +84,48 @@ __global__ void __launch_bounds__(256) k_inv_partial(long long n, const float4* 
     const long long b1 = b0 + per < n ? b0 + per : n;
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
     float hi[7] = {0, 0, 0, 0, 0, 0, 0}, lo[7] = {0, 0, 0, 0, 0, 0, 0};
+    // rows in the same order as one row per loop trip, with the loads of
+    // kInvRows rows issued together (the sums' dependency chains would
+    // otherwise leave one row's loads in flight per thread)
     int k = 0;
-    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        if (vel) {
-            const float4 v = vel[i];
-            df_add(hi[0], lo[0], v.x);
-            df_add(hi[1], lo[1], v.y);
-            df_add(hi[2], lo[2], v.z);
-            const float px = __fmul_rn(v.x, v.x), py = __fmul_rn(v.y, v.y), pz = __fmul_rn(v.z, v.z);
-            df_add(hi[6], lo[6], px);
-            df_add(hi[6], lo[6], py);
-            df_add(hi[6], lo[6], pz);
-            // the products' exact rounding errors (tiny: one plain add each)
-            lo[6] = __fadd_rn(lo[6], __fadd_rn(__fmaf_rn(v.x, v.x, -px),
-                                               __fadd_rn(__fmaf_rn(v.y, v.y, -py), __fmaf_rn(v.z, v.z, -pz))));
-        }
-        if (acc) {
-            const float4 a = acc[i];
-            df_add(hi[3], lo[3], a.x);
-            df_add(hi[4], lo[4], a.y);
-            df_add(hi[5], lo[5], a.z);
-        }
-        if (++k == kInvFold) {
+    for (long long i0 = b0 + threadIdx.x; i0 < b1; i0 += (long long)kInvRows * blockDim.x) {
+        float4 vr[kInvRows], ar[kInvRows];
 #pragma unroll
-            for (int c = 0; c < 7; ++c) {
-                s[c] += (double)hi[c] + (double)lo[c];
-                hi[c] = lo[c] = 0.f;
+        for (int r = 0; r < kInvRows; ++r) {
+            const long long i = i0 + (long long)r * blockDim.x;
+            vr[r] = vel && i < b1 ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            ar[r] = acc && i < b1 ? acc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < kInvRows; ++r) {
+            if (i0 + (long long)r * blockDim.x >= b1) break;
+            if (vel) {
+                const float4 v = vr[r];
+                df_add(hi[0], lo[0], v.x);
+                df_add(hi[1], lo[1], v.y);
+                df_add(hi[2], lo[2], v.z);
+                const float px = __fmul_rn(v.x, v.x), py = __fmul_rn(v.y, v.y), pz = __fmul_rn(v.z, v.z);
+                df_add(hi[6], lo[6], px);
+                df_add(hi[6], lo[6], py);
+                df_add(hi[6], lo[6], pz);
+                // the products' exact rounding errors (tiny: one plain add each)
+                lo[6] = __fadd_rn(lo[6], __fadd_rn(__fmaf_rn(v.x, v.x, -px),
+                                                   __fadd_rn(__fmaf_rn(v.y, v.y, -py), __fmaf_rn(v.z, v.z, -pz))));
             }
-            k = 0;
+            if (acc) {
+                const float4 a = ar[r];
+                df_add(hi[3], lo[3], a.x);
+                df_add(hi[4], lo[4], a.y);
+                df_add(hi[5], lo[5], a.z);
+            }
+            if (++k == kInvFold) {
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    s[c] += (double)hi[c] + (double)lo[c];
+                    hi[c] = lo[c] = 0.f;
+                }
+                k = 0;
+            }
         }
     }
 #pragma unroll

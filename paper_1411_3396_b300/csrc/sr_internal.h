@@ -271,6 +271,18 @@ struct sr_plan {
     cudaStream_t h_side = nullptr;      // sr_step_host: velocity upload beside the binning
     cudaEvent_t h_fork = nullptr, h_join = nullptr;
 
+    // staging for sr_step_host_submit: two sets used in turn, so that one
+    // step's uploads run while the step before it computes
+    double* q_pos[2] = {nullptr, nullptr};
+    float* q_vel[2] = {nullptr, nullptr};
+    float* q_acc[2] = {nullptr, nullptr};
+    cudaStream_t q_up = nullptr, q_down = nullptr;    // host-to-device and device-to-host copies
+    cudaEvent_t q_loaded[2] = {nullptr, nullptr};     // a set's uploads done
+    cudaEvent_t q_computed[2] = {nullptr, nullptr};   // its step's force and kick done
+    cudaEvent_t q_freed[2] = {nullptr, nullptr};      // its downloads done: the set may be refilled
+    bool q_used[2] = {false, false};
+    int q_next = 0;
+
     int sm_count = 0;
     int variant = 0;                       // pair-kernel variant (launch bounds), see force.cu
     int force_blocks = 0;

@@ -142,6 +142,52 @@ def test_step_host_matches_device_path():
         assert vh.numpy().tobytes() == to_np(vd).tobytes()
 
 
+def test_step_host_submit_pipelined_matches_step_host():
+    # five independent inputs (distinct positions and velocities) submitted
+    # back to back with their own page-locked buffers: up to two steps in
+    # flight on the two staging sets; every step's accelerations and kicked
+    # velocities equal the synchronous sr_step_host's bit for bit, also for
+    # a step submitted without an acceleration buffer
+    w = wc.make_workload(wc.small_variant("zeldovich128"))
+    (pos, box), = w["volumes"]
+    prm = w["params"]
+    n = len(pos)
+    rng = np.random.default_rng(7)
+    inputs = []
+    for k in range(5):
+        p = np.mod(pos + rng.normal(0.0, 0.2 * k, pos.shape), box)
+        v = np.zeros((n, 4), np.float32)
+        v[:, :3] = rng.normal(0.0, 1.0, (n, 3))
+        inputs.append((p, v))
+    ref = make_plan(w["volumes"], prm)
+    expect = []
+    for p, v in inputs:
+        vh = torch.from_numpy(v.copy()).pin_memory()
+        ah = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+        ref.step_host(torch.from_numpy(p).pin_memory(), vh, ah, prm["dt"])
+        expect.append((ah.numpy().copy(), vh.numpy().copy()))
+    plan = make_plan(w["volumes"], prm)
+    bufs = [(torch.from_numpy(p).pin_memory(), torch.from_numpy(v.copy()).pin_memory(),
+             torch.full((n, 4), np.nan, dtype=torch.float32).pin_memory()) for p, v in inputs]
+    for k, (ph, vh, ah) in enumerate(bufs):
+        plan.step_host_submit(ph, vh, None if k == 3 else ah, prm["dt"])
+    plan.step_host_wait()
+    for k, ((_, vh, ah), (a_ref, v_ref)) in enumerate(zip(bufs, expect)):
+        assert vh.numpy().tobytes() == v_ref.tobytes(), k
+        if k == 3:
+            assert np.isnan(ah.numpy()).all()
+        else:
+            assert ah.numpy().tobytes() == a_ref.tobytes(), k
+    # a second round on the same plan after the wait reuses the staging sets
+    ph, vh, ah = bufs[0]
+    vh.copy_(torch.from_numpy(inputs[0][1]))
+    plan.step_host_submit(ph, vh, ah, prm["dt"])
+    plan.step_host_wait()
+    assert vh.numpy().tobytes() == expect[0][1].tobytes()
+    assert ah.numpy().tobytes() == expect[0][0].tobytes()
+    plan.status()
+
+
 def test_batch_full_size_graph_and_sampled_oracle():
     # the 64-volume batched workload under one captured graph; rows of a few
     # volumes checked against the oracle
