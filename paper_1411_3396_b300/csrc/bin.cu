@@ -88,6 +88,45 @@ __device__ __forceinline__ double quotient_rn_normal(double x, double h, double 
     return fma(fma(-q, h, x), y, q);
 }
 
+// The same correctly rounded quotient from the product alone and one exact
+// integer step, for x in [2^-900, box) and h not a power of two.
+// q0 = RN(x y) lies within 1.5 ulp of x / h, so RN(x / h) is q0 or one of
+// its two neighbours: which one follows from comparing x / h with the
+// midpoints next to q0, that is x = Mx 2^Ex with m h = (2 Mq +- 1) Mh
+// 2^(Eq - 1 + Eh) (integer significands, products in 128 bits).  Below a
+// power of two the lower neighbour is half an ulp away, so that midpoint is
+// (4 Mq - 1) 2^(Eq - 2).  No midpoint can equal x / h exactly: Mh has an
+// odd factor above 1 and 2 Mq +- 1 is odd and above 2^53, so their product
+// is no 53-bit significand times a power of two.  One binary64 operation
+// and integer arithmetic, against five binary64 operations for the
+// corrections above (B300 runs binary64 at 1/64 of its binary32 rate).
+__device__ __forceinline__ double quotient_rn_int(double x, double h, double y) {
+    constexpr unsigned long long kMant = (1ull << 52) - 1ull, kHidden = 1ull << 52;
+    const double q0 = x * y;
+    const unsigned long long ux = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long uq = (unsigned long long)__double_as_longlong(q0);
+    const unsigned long long uh = (unsigned long long)__double_as_longlong(h);
+    const unsigned long long mx = (ux & kMant) | kHidden, mq = (uq & kMant) | kHidden;
+    const unsigned long long mh = (uh & kMant) | kHidden;
+    const int s = (int)(ux >> 52) - (int)(uq >> 52) - (int)(uh >> 52) + 1076;   // Ex - Eq - Eh + 1, in [52, 55]
+    const unsigned long long xl = mx << s, xh = mx >> (64 - s);                  // x as Mx 2^s
+    const unsigned long long a = 2ull * mq + 1ull;                                 // upper midpoint
+    const unsigned long long pl = a * mh, ph = __umul64hi(a, mh);
+    const bool up = xh > ph || (xh == ph && xl > pl);
+    bool down;
+    if (mq != kHidden) {                                                           // (2 Mq - 1) Mh = P - 2 Mh
+        const unsigned long long d = 2ull * mh;
+        const unsigned long long ll = pl - d, lh = ph - (pl < d ? 1ull : 0ull);
+        down = xh < lh || (xh == lh && xl < ll);
+    } else {                                                                       // q0 a power of two
+        const unsigned long long b = 4ull * mq - 1ull;
+        const unsigned long long ll = b * mh, lh = __umul64hi(b, mh);
+        const unsigned long long yl = xl << 1, yh = (xh << 1) | (xl >> 63);
+        down = yh < lh || (yh == lh && yl < ll);
+    }
+    return __longlong_as_double((long long)(uq + (up ? 1ull : 0ull) - (down ? 1ull : 0ull)));
+}
+
 __device__ __forceinline__ double quotient_rn(double x, double h, double y) {
     return x < 0x1p-900 ? x / h : quotient_rn_normal(x, h, y);
 }
@@ -104,7 +143,7 @@ __device__ __forceinline__ bool fine_axis_quot(double x, unsigned long long ubox
                                                unsigned long long& mant, int& F) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     if (u >= ubox || u < (123ull << 52)) return false;       // outside [2^-900, box)
-    const double t = quotient_rn_normal(x, h, y);
+    const double t = quotient_rn_int(x, h, y);
     const unsigned long long ut = (unsigned long long)__double_as_longlong(t);
     const int E = (int)(ut >> 52) - 1023;                     // t >= 0: sign bit clear
     if (E < 0) {                                              // t < 1 (zero or subnormal included)

@@ -8,7 +8,9 @@ value once), must equal the IEEE binary64 division x / h.  The theorem's
 premises are checked as well: q1 within one ulp of x / h and the last
 residual exact.  Inputs cover random positions, quotients below 1 and
 positions a few ulps either side of the faces k h, where a wrong rounding
-would change the fine cell."""
+would change the fine cell.  The chunk kernel's form, the product and one
+step to a neighbour decided on exact integer midpoints, is checked on the
+same inputs and next to powers of two."""
 import math
 from fractions import Fraction as Fr
 
@@ -106,3 +108,62 @@ def test_floor_from_one_product_matches_the_division():
                 taken += 1
                 assert q == math.floor(t_rn), (box, M, x)
     assert taken > 15000 and declined > 500
+
+
+def _bits(v):
+    return int(np.float64(v).view(np.uint64))
+
+
+def _from_bits(u):
+    return float(np.uint64(u).view(np.float64))
+
+
+def _quotient_one_step(x, h, y):
+    """The chunk kernel's quotient: q0 = RN(x y), then one step to a
+    neighbour decided in integers, comparing x / h with the midpoints next
+    to q0 (x = Mx 2^Ex, m h = (2 Mq +- 1) Mh 2^(Eq - 1 + Eh), below a power
+    of two (4 Mq - 1) Mh 2^(Eq - 2)), as the kernel does in 128 bits."""
+    mant, hidden = (1 << 52) - 1, 1 << 52
+    q0 = x * y
+    ux, uq, uh = _bits(x), _bits(q0), _bits(h)
+    mx, mq, mh = (ux & mant) | hidden, (uq & mant) | hidden, (uh & mant) | hidden
+    s = (ux >> 52) - (uq >> 52) - (uh >> 52) + 1076
+    assert 52 <= s <= 55
+    big = mx << s                                   # x in units of 2^(Eq - 1 + Eh)
+    up = big > (2 * mq + 1) * mh
+    if mq != hidden:
+        down = big < (2 * mq - 1) * mh
+    else:
+        down = (big << 1) < (4 * mq - 1) * mh
+    assert (big << 1) != (4 * mq - 1) * mh and big != (2 * mq + 1) * mh and big != (2 * mq - 1) * mh
+    return _from_bits(uq + int(up) - int(down))
+
+
+def test_one_integer_step_quotient_equals_ieee_division():
+    # RN(x / h) from the product and one step decided on exact integer
+    # midpoints; the same inputs as the corrected quotient above, plus
+    # quotients next to powers of two (where the lower neighbour is half an
+    # ulp away) and every position within two ulps of them
+    rng = np.random.default_rng(31)
+    boxes = [23.0, 98.0, 17.0, 30.0, 1000.0 / 3.0, 0.7, 3.3e5] + list(rng.uniform(6.0, 600.0, 5))
+    n = moved = 0
+    for box in boxes:
+        for M in (max(1, int(box // 4)) << 6, 13, 1000):
+            h, xs = _cases(rng, box, M)
+            if h == 2.0 ** math.floor(math.log2(h)):
+                continue                               # powers of two take the exact scaling
+            y = float(1 / Fr(h))
+            for k in range(-8, 24):                    # x / h near 2^k
+                x0 = float(Fr(2) ** k * Fr(h))
+                for d in range(-2, 3):
+                    x = x0
+                    for _ in range(abs(d)):
+                        x = float(np.nextafter(x, np.inf if d > 0 else -np.inf))
+                    if 2.0 ** -900 <= x < box:
+                        xs.append(x)
+            for x in xs:
+                t = _quotient_one_step(x, h, y)
+                assert t == x / h, (box, M, x)
+                moved += t != x * y
+                n += 1
+    assert n > 20000 and moved > 1000
