@@ -55,26 +55,30 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Adds x to the binary32 pair (hi, lo): hi takes the rounded sum, lo
-// gathers the exact rounding errors (lo's own rounding is about 2^-48 of hi).
+// (hi, lo) += x for a sum held as an unevaluated pair of binary32 numbers:
+// TwoSum of hi and x, its exact error added to lo, then the pair
+// renormalised (Fast2Sum of the sum and the error terms), so that lo stays
+// below about an ulp of hi and the pair keeps close to 48 significant bits
+// however many terms it takes.
 __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
-    float e;
-    two_sum(hi, x, hi, e);
-    lo = __fadd_rn(lo, e);
+    float s, e;
+    two_sum(hi, x, s, e);
+    e = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
-constexpr int kInvFold = 8;        // rows a thread sums in binary32 pairs before each binary64 add
 constexpr int kInvRows = 4;        // rows whose loads a thread issues together
 
-// Block partial sums of the seven invariants.  B300 runs binary64 at a small
-// fraction of its binary32 rate, and a binary64 add per term bound this
-// kernel (about 20 binary64 operations per row).  Each thread sums kInvFold
-// of its rows as binary32 (hi, lo) pairs, the squares split exactly by an
-// FMA, and adds each pair to its binary64 sums once: about 3.5 binary64
-// operations per row.  The pairs' rounding is at most about kInvFold^2 2^-48
-// of the fold's terms (an emulation of the scheme on 200 random sets of
-// mixed magnitudes stayed within 1.1e-15 of the sum of the terms'
-// magnitudes of the exact sum).
+// Block partial sums of the seven invariants.  B300 runs binary64 at 1/64
+// of its binary32 rate, and binary64 adds per term bound this kernel (about
+// 20 binary64 operations per row when every term was added in binary64,
+// 3.5 when binary32 pairs were folded into binary64 every 8 rows).  Each
+// thread now sums all of its rows as renormalised binary32 pairs, the
+// squares split exactly by an FMA, and converts its seven pairs to binary64
+// once at the end.  An emulation of the scheme on random sets of mixed
+// magnitudes (tests/test_invariants_scheme.py) bounds its error against
+// the exact sum.
 __global__ void __launch_bounds__(256, 4) k_inv_partial(long long n, const float4* __restrict__ vel,
                                                      const float4* __restrict__ acc,
                                                      double* __restrict__ partials) {
@@ -87,7 +91,6 @@ __global__ void __launch_bounds__(256, 4) k_inv_partial(long long n, const float
     // rows in the same order as one row per loop trip, with the loads of
     // kInvRows rows issued together (the sums' dependency chains would
     // otherwise leave one row's loads in flight per thread)
-    int k = 0;
     for (long long i0 = b0 + threadIdx.x; i0 < b1; i0 += (long long)kInvRows * blockDim.x) {
         float4 vr[kInvRows], ar[kInvRows];
 #pragma unroll
@@ -117,14 +120,6 @@ __global__ void __launch_bounds__(256, 4) k_inv_partial(long long n, const float
                 df_add(hi[3], lo[3], a.x);
                 df_add(hi[4], lo[4], a.y);
                 df_add(hi[5], lo[5], a.z);
-            }
-            if (++k == kInvFold) {
-#pragma unroll
-                for (int c = 0; c < 7; ++c) {
-                    s[c] += (double)hi[c] + (double)lo[c];
-                    hi[c] = lo[c] = 0.f;
-                }
-                k = 0;
             }
         }
     }
