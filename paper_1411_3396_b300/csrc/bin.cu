@@ -219,6 +219,7 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
 }
 
 constexpr int kSmallCell = 128;                 // ranges sorted by one warp in registers (bitonic)
+static_assert(kSmallCell <= 128, "a position in a small range takes 7 bits of the 32-bit sort key");
 constexpr int kWarpSeg = 512;                   // ranges sorted by one warp in shared memory (LSD)
 constexpr int kWarpRounds = kWarpSeg / 32;
 constexpr int kSegTile = 2048;                  // elements a block-sort holds in shared memory
@@ -261,8 +262,8 @@ __device__ __forceinline__ int block_exclusive_scan256(int v, int* warp_tot) {
 
 // Bitonic sort of 32 S values held as v[s] at lane l (element l + 32 s),
 // ascending.
-template <int S>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[S]) {
+template <int S, class T>
+__device__ __forceinline__ void warp_bitonic(T (&v)[S]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 2; k <= 32 * S; k <<= 1) {
@@ -274,7 +275,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[S]) {
                 for (int s = 0; s < S; ++s) {
                     if (s & js) continue;
                     const bool asc = ((lane + 32 * s) & k) == 0;
-                    const unsigned long long x = v[s], y = v[s | js];
+                    const T x = v[s], y = v[s | js];
                     if ((x > y) == asc) {
                         v[s] = y;
                         v[s | js] = x;
@@ -283,9 +284,9 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[S]) {
             } else {
 #pragma unroll
                 for (int s = 0; s < S; ++s) {
-                    const unsigned long long y = __shfl_xor_sync(kFull, v[s], j);
+                    const T y = __shfl_xor_sync(kFull, v[s], j);
                     const bool asc = ((lane + 32 * s) & k) == 0, lower = (lane & j) == 0;
-                    const unsigned long long lo = v[s] < y ? v[s] : y, hi = v[s] < y ? y : v[s];
+                    const T lo = v[s] < y ? v[s] : y, hi = v[s] < y ? y : v[s];
                     v[s] = lower == asc ? lo : hi;
                 }
             }
@@ -301,23 +302,54 @@ __device__ __forceinline__ void load_small(const unsigned long long* src, int m,
     for (int s = 0; s < 4; ++s) v[s] = m <= kSmallCell && lane + 32 * s < m ? src[lane + 32 * s] : ~0ull;
 }
 
+// Sorts the preloaded composites of a range of m <= 32 S values into dst:
+// a bitonic sort of 32-bit keys (Morton code << 7 | position in the range:
+// 3 b + 7 <= 31 bits) instead of the 64-bit composites, then each output
+// takes its composite from the position in its key (S shuffles).  Equal
+// Morton codes (particles in one fine cell) leave such a run ordered by
+// position, not caller index; if the range has one, the gathered
+// composites are sorted again in full.
 template <int S>
-__device__ __forceinline__ void warp_sort_store_s(const unsigned long long (&in)[4], unsigned long long* dst, int m) {
+__device__ __forceinline__ void warp_sort_store_s(const unsigned long long (&in)[4], unsigned long long* dst, int m,
+                                                  int ib) {
     const int lane = threadIdx.x & 31;
-    unsigned long long v[S];
+    unsigned k[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) v[s] = in[s];
-    warp_bitonic<S>(v);
+    for (int s = 0; s < S; ++s) {
+        const int e = lane + 32 * s;
+        k[s] = e < m ? ((unsigned)(in[s] >> ib) << 7) | (unsigned)e : 0xffffffffu;
+    }
+    warp_bitonic<S>(k);
+    unsigned long long v[S];
+    bool tie = false;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int p = (int)(k[s] & 127u);
+        unsigned long long c = ~0ull;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const unsigned long long g = __shfl_sync(kFull, in[t], p & 31);
+            if ((p >> 5) == t) c = g;
+        }
+        const int o = lane + 32 * s;
+        v[s] = o < m ? c : ~0ull;
+        const unsigned up = __shfl_up_sync(kFull, k[s], 1);
+        const unsigned wrap = __shfl_sync(kFull, k[s > 0 ? s - 1 : 0], 31);
+        const unsigned prev = lane > 0 ? up : wrap;
+        tie = tie || (o < m && o > 0 && (prev >> 7) == (k[s] >> 7));
+    }
+    if (__any_sync(kFull, tie)) warp_bitonic<S>(v);
 #pragma unroll
     for (int s = 0; s < S; ++s)
         if (lane + 32 * s < m) dst[lane + 32 * s] = v[s];
 }
 
 // Sorts the preloaded values of a range of m <= kSmallCell into dst.
-__device__ __forceinline__ void warp_sort_store(const unsigned long long (&v)[4], unsigned long long* dst, int m) {
-    if (m <= 32) warp_sort_store_s<1>(v, dst, m);
-    else if (m <= 64) warp_sort_store_s<2>(v, dst, m);
-    else warp_sort_store_s<4>(v, dst, m);
+__device__ __forceinline__ void warp_sort_store(const unsigned long long (&v)[4], unsigned long long* dst, int m,
+                                                int ib) {
+    if (m <= 32) warp_sort_store_s<1>(v, dst, m, ib);
+    else if (m <= 64) warp_sort_store_s<2>(v, dst, m, ib);
+    else warp_sort_store_s<4>(v, dst, m, ib);
 }
 
 // Shared-memory counters ctr[key] += 1 for every lane with ok, one atomic
@@ -883,7 +915,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) k_sort_segments(unsigned long 
         const int4 sn2 = entry(item + 2 * stride);
         unsigned long long nv[4];
         load_small((sn.z ? scratch : comp) + sn.x, sn.y, nv);
-        if (sg.y <= kSmallCell) warp_sort_store(pv, comp + sg.x, sg.y);
+        if (sg.y <= kSmallCell) warp_sort_store(pv, comp + sg.x, sg.y, ib);
         else warp_lsd((sg.z ? scratch : comp) + sg.x, comp + sg.x, sg.y, sg.w, ib, sv + 2 * warp * kWarpSeg, wh[warp]);
         item += stride;
         sg = sn;

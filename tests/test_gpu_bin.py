@@ -203,7 +203,17 @@ def test_bin_tie_runs_each_sort_path(chunk):
         (6000, [0.85, 0.35, 0.35], [2, 32]),
         (6000, [0.85, 0.35, 0.35], [33, 3]),
     ]
+    # ranges of up to 128 sorted in registers on 32-bit keys (Morton code,
+    # position): without runs, and with runs that send the range to the
+    # full 64-bit sort (second row of cells)
+    small = [(20, 3.6, []), (40, 3.6, [2, 5]), (64, 3.6, [2]), (100, 3.6, [3, 32]), (128, 3.6, [2, 2, 2])]
     parts = []
+    for k, (m, ext, runs) in enumerate(small):
+        corner = np.array([k * side, 4 * side, 0.0])
+        rng = np.random.default_rng(90 + k)
+        parts.append(corner + 0.1 + rng.random((m - sum(runs), 3)) * ext)
+        for j, r in enumerate(runs):
+            parts.append(np.tile(corner + [0.11 + 0.1 * j, 0.02, 0.02], (r, 1)))
     for k, (m, ext, runs) in enumerate(cells):
         corner = np.array([k * side, 2 * side, 0.0])
         rng = np.random.default_rng(60 + k)
