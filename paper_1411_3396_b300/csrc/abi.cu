@@ -509,16 +509,13 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
     if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
     cudaStream_t st = as_stream(stream);
     int rc;
-    if (!p->h_pos_dev) {
-        if ((rc = dalloc(&p->h_pos_dev, (size_t)p->capacity * 3)) || (rc = dalloc(&p->h_vel_dev, (size_t)p->capacity * 4)) ||
-            (rc = dalloc(&p->h_acc_dev, (size_t)p->capacity * 4)))
-            return rc;
-    }
-    if (!p->h_side) {
-        SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->h_side, cudaStreamNonBlocking));
-        SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->h_fork, cudaEventDisableTiming));
-        SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->h_join, cudaEventDisableTiming));
-    }
+    if ((!p->h_pos_dev && (rc = dalloc(&p->h_pos_dev, (size_t)p->capacity * 3))) ||
+        (!p->h_vel_dev && (rc = dalloc(&p->h_vel_dev, (size_t)p->capacity * 4))) ||
+        (!p->h_acc_dev && (rc = dalloc(&p->h_acc_dev, (size_t)p->capacity * 4))))
+        return rc;
+    if (!p->h_side) SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->h_side, cudaStreamNonBlocking));
+    if (!p->h_fork) SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->h_fork, cudaEventDisableTiming));
+    if (!p->h_join) SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->h_join, cudaEventDisableTiming));
     // The velocity upload runs on a side stream after the position upload
     // (both share the host link, and the binning needs the positions first),
     // beside the binning; the force kernel (which reads the velocities in the
@@ -545,16 +542,17 @@ int sr_step_host_submit(sr_plan* p, const double* pos, float* vel, float* acc, f
     if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
     cudaStream_t st = as_stream(stream);
     int rc;
-    if (!p->q_up) {
+    if (!p->q_up) {                      // first call; a failed one is resumed where it stopped
         for (int k = 0; k < 2; ++k) {
-            if ((rc = dalloc(&p->q_pos[k], (size_t)p->capacity * 3)) || (rc = dalloc(&p->q_vel[k], (size_t)p->capacity * 4)) ||
-                (rc = dalloc(&p->q_acc[k], (size_t)p->capacity * 4)))
+            if ((!p->q_pos[k] && (rc = dalloc(&p->q_pos[k], (size_t)p->capacity * 3))) ||
+                (!p->q_vel[k] && (rc = dalloc(&p->q_vel[k], (size_t)p->capacity * 4))) ||
+                (!p->q_acc[k] && (rc = dalloc(&p->q_acc[k], (size_t)p->capacity * 4))))
                 return rc;
-            SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_loaded[k], cudaEventDisableTiming));
-            SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_computed[k], cudaEventDisableTiming));
-            SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_freed[k], cudaEventDisableTiming));
+            if (!p->q_loaded[k]) SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_loaded[k], cudaEventDisableTiming));
+            if (!p->q_computed[k]) SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_computed[k], cudaEventDisableTiming));
+            if (!p->q_freed[k]) SR_CUDA_CHECK(cudaEventCreateWithFlags(&p->q_freed[k], cudaEventDisableTiming));
         }
-        SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->q_down, cudaStreamNonBlocking));
+        if (!p->q_down) SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->q_down, cudaStreamNonBlocking));
         SR_CUDA_CHECK(cudaStreamCreateWithFlags(&p->q_up, cudaStreamNonBlocking));
     }
     const int s = p->q_next;
