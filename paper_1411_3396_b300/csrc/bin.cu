@@ -549,8 +549,9 @@ __global__ void __launch_bounds__(256) k_keys(const double* __restrict__ pos, in
 }
 
 // Cell starts and chunk starts from the counts (both exclusive scans, cell
-// total_cells holding the totals), the chunk -> cell map, and the lists of
-// cells to sort by block.  A tile of 2048 cells per block; the tile's
+// total_cells holding the totals), each chunk's record (cell, first sorted
+// row, count, volume), and the lists of cells to sort by warp, by block or
+// to split.  A tile of 2048 cells per block; the tile's
 // prefix comes from the tiles before it by a decoupled look-back over
 // words holding (flag, particle sum, chunk sum) in (2, 31, 31) bits.
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(
