@@ -370,8 +370,10 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  *           copies are done; copy the updated vel and, if acc is not null,
  *           the accelerations (host float4 rows) back on a plan-owned
  *           download stream.  Steps run on `stream` in submission order
- *           (they share the plan's workspace).  The results are the same
- *           bits as sr_step_host's for the same inputs.
+ *           (they share the plan's workspace), so every submit to a plan
+ *           must name the same stream, as must other calls on the plan
+ *           while steps are in flight.  The results are the same bits as
+ *           sr_step_host's for the same inputs.
  *   wait:   blocks until every submitted step's read-back is done.
  * The host buffers of a step must stay valid and unchanged until its
  * read-back is done (sr_step_host_wait, or two submits later, when its
