@@ -380,9 +380,10 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  * staging set is reused); pos is read, vel is read and then overwritten.
  * Page-locked host buffers are needed for the copies to overlap.  The first
  * submit allocates the two staging sets (2 x 56 bytes per particle of the
- * plan's capacity), two streams and six events.  Errors: SR_ERR_ARG (null
- * plan or buffer), SR_ERR_CAPACITY (n above the capacity), those of sr_bin
- * and sr_force_kick, SR_ERR_CUDA.
+ * plan's capacity), two streams and six events.  n = 0 copies nothing (the
+ * buffers may then be null).  Errors: SR_ERR_ARG (null plan, or a null
+ * buffer with n > 0), SR_ERR_CAPACITY (n above the capacity), those of
+ * sr_bin and sr_force_kick, SR_ERR_CUDA.
  */
 int sr_step_host_submit(sr_plan* plan, const double* pos, float* vel, float* acc, float dt,
                         int64_t n, void* stream);

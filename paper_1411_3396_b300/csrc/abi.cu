@@ -538,7 +538,7 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
 
 int sr_step_host_submit(sr_plan* p, const double* pos, float* vel, float* acc, float dt, int64_t n, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
-    if (!pos || !vel) return set_error(SR_ERR_ARG, "null host buffer");
+    if ((!pos || !vel) && n > 0) return set_error(SR_ERR_ARG, "null host buffer");
     if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
     cudaStream_t st = as_stream(stream);
     int rc;
@@ -558,8 +558,10 @@ int sr_step_host_submit(sr_plan* p, const double* pos, float* vel, float* acc, f
     const int s = p->q_next;
     // uploads into set s once the step that used it last has been read back
     if (p->q_used[s]) SR_CUDA_CHECK(cudaStreamWaitEvent(p->q_up, p->q_freed[s], 0));
-    SR_CUDA_CHECK(cudaMemcpyAsync(p->q_pos[s], pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, p->q_up));
-    SR_CUDA_CHECK(cudaMemcpyAsync(p->q_vel[s], vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, p->q_up));
+    if (n > 0) {
+        SR_CUDA_CHECK(cudaMemcpyAsync(p->q_pos[s], pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, p->q_up));
+        SR_CUDA_CHECK(cudaMemcpyAsync(p->q_vel[s], vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, p->q_up));
+    }
     SR_CUDA_CHECK(cudaEventRecord(p->q_loaded[s], p->q_up));
     // binning and force on the caller's stream, after the step before (the
     // plan's workspace) and after this set's uploads
@@ -568,8 +570,11 @@ int sr_step_host_submit(sr_plan* p, const double* pos, float* vel, float* acc, f
     if ((rc = launch_force(p, p->q_acc[s], nullptr, nullptr, st, p->q_vel[s], dt))) return rc;
     SR_CUDA_CHECK(cudaEventRecord(p->q_computed[s], st));
     SR_CUDA_CHECK(cudaStreamWaitEvent(p->q_down, p->q_computed[s], 0));
-    SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->q_vel[s], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, p->q_down));
-    if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->q_acc[s], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, p->q_down));
+    if (n > 0) {
+        SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->q_vel[s], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, p->q_down));
+        if (acc)
+            SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->q_acc[s], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, p->q_down));
+    }
     SR_CUDA_CHECK(cudaEventRecord(p->q_freed[s], p->q_down));
     p->q_used[s] = true;
     p->q_next = 1 - s;

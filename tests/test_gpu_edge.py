@@ -60,3 +60,34 @@ def test_empty_fof_and_pm():
     assert torch.isfinite(pk).all()
     pm.close()
     plan.close()
+
+
+def test_host_step_submit_arguments_and_empty():
+    # the pipelined host step: an empty step, a step above the capacity
+    # (refused before any copy is enqueued), null buffers through the C ABI,
+    # and a wait with nothing submitted
+    import ctypes
+
+    from paper_1411_3396_b300 import Plan
+    from paper_1411_3396_b300._lib import SrError, load
+    plan = Plan(16.0, 3.0, 0.1, 0.8, 1000)
+    plan.step_host_wait()                               # nothing submitted: returns at once
+    p0 = torch.zeros((0, 3), dtype=torch.float64).pin_memory()
+    v0 = torch.zeros((0, 4), dtype=torch.float32).pin_memory()
+    plan.step_host_submit(p0, v0, None, 0.01)
+    plan.step_host_wait()
+    big = torch.zeros((1001, 3), dtype=torch.float64).pin_memory()
+    vbig = torch.zeros((1001, 4), dtype=torch.float32).pin_memory()
+    with pytest.raises(SrError) as e:
+        plan.step_host_submit(big, vbig, None, 0.01)
+    assert e.value.code == 3                            # SR_ERR_CAPACITY
+    assert load().sr_step_host_submit(plan._h, None, None, None, ctypes.c_float(0.01), 10, None) == 1
+    assert load().sr_step_host_wait(None) == 1
+    # a real step after the refusals
+    pos = torch.from_numpy(gen.uniform_box(500, 16.0, 5)).pin_memory()
+    vel = torch.zeros((500, 4), dtype=torch.float32).pin_memory()
+    acc = torch.zeros((500, 4), dtype=torch.float32).pin_memory()
+    plan.step_host_submit(pos, vel, acc, 0.01)
+    plan.step_host_wait()
+    assert torch.isfinite(acc).all() and acc.abs().sum() > 0
+    plan.close()
