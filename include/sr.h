@@ -353,7 +353,7 @@ int sr_plan_copy(sr_plan* plan, int which, void* dst, int64_t bytes, void* strea
  * runs on a plan-owned side stream after the position upload, beside the
  * binning (the force waits for it).  Host buffers should be page-locked for
  * overlap.  The first call allocates the staging buffers, the side stream
- * and two events.
+ * and two events.  n = 0 copies nothing (the buffers may then be null).
  */
 int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float dt,
                  int64_t n, void* stream);

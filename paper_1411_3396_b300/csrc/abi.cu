@@ -505,7 +505,7 @@ int sr_plan_copy(sr_plan* p, int which, void* dst, int64_t bytes, void* stream) 
 
 int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt, int64_t n, void* stream) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
-    if (!pos || !vel) return set_error(SR_ERR_ARG, "null host buffer");
+    if ((!pos || !vel) && n > 0) return set_error(SR_ERR_ARG, "null host buffer");
     if (n < 0 || n > p->capacity) return set_error(SR_ERR_CAPACITY, "n exceeds the plan capacity");
     cudaStream_t st = as_stream(stream);
     int rc;
@@ -520,18 +520,21 @@ int sr_step_host(sr_plan* p, const double* pos, float* vel, float* acc, float dt
     // (both share the host link, and the binning needs the positions first),
     // beside the binning; the force kernel (which reads the velocities in the
     // fused kick) waits for it.
-    SR_CUDA_CHECK(cudaMemcpyAsync(p->h_pos_dev, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    if (n > 0) SR_CUDA_CHECK(cudaMemcpyAsync(p->h_pos_dev, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     SR_CUDA_CHECK(cudaEventRecord(p->h_fork, st));
     SR_CUDA_CHECK(cudaStreamWaitEvent(p->h_side, p->h_fork, 0));
-    SR_CUDA_CHECK(cudaMemcpyAsync(p->h_vel_dev, vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, p->h_side));
+    if (n > 0)
+        SR_CUDA_CHECK(cudaMemcpyAsync(p->h_vel_dev, vel, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, p->h_side));
     SR_CUDA_CHECK(cudaEventRecord(p->h_join, p->h_side));
     rc = sr_bin(p, p->h_pos_dev, n, stream);
     cudaError_t we = cudaStreamWaitEvent(st, p->h_join, 0);       // join even when sr_bin failed
     if (rc) return rc;
     if (we != cudaSuccess) return cuda_fail(we, "sr_step_host");
     if ((rc = launch_force(p, p->h_acc_dev, nullptr, nullptr, st, p->h_vel_dev, dt))) return rc;
-    SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->h_vel_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
-    if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
+    if (n > 0) {
+        SR_CUDA_CHECK(cudaMemcpyAsync(vel, p->h_vel_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
+        if (acc) SR_CUDA_CHECK(cudaMemcpyAsync(acc, p->h_acc_dev, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, st));
+    }
     SR_CUDA_CHECK(cudaStreamSynchronize(st));
     return SR_OK;
 }

@@ -76,6 +76,7 @@ def test_host_step_submit_arguments_and_empty():
     v0 = torch.zeros((0, 4), dtype=torch.float32).pin_memory()
     plan.step_host_submit(p0, v0, None, 0.01)
     plan.step_host_wait()
+    plan.step_host(p0, v0, None, 0.01)                  # the synchronous form as well
     big = torch.zeros((1001, 3), dtype=torch.float64).pin_memory()
     vbig = torch.zeros((1001, 4), dtype=torch.float32).pin_memory()
     with pytest.raises(SrError) as e:
