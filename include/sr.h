@@ -374,7 +374,9 @@ int sr_step_host(sr_plan* plan, const double* pos, float* vel, float* acc, float
  *           must name the same stream, as must other calls on the plan
  *           while steps are in flight.  The results are the same bits as
  *           sr_step_host's for the same inputs.
- *   wait:   blocks until every submitted step's read-back is done.
+ *   wait:   blocks until every submitted step's read-back is done, and
+ *           every upload, also those of a submit that returned an error
+ *           after enqueuing them (its host buffers are read until then).
  * The host buffers of a step must stay valid and unchanged until its
  * read-back is done (sr_step_host_wait, or two submits later, when its
  * staging set is reused); pos is read, vel is read and then overwritten.

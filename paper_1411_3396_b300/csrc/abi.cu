@@ -586,8 +586,10 @@ int sr_step_host_submit(sr_plan* p, const double* pos, float* vel, float* acc, f
 
 int sr_step_host_wait(sr_plan* p) {
     if (!p) return set_error(SR_ERR_ARG, "plan is null");
-    if (!p->q_down) return SR_OK;                    // nothing submitted
-    SR_CUDA_CHECK(cudaStreamSynchronize(p->q_down));
+    // the uploads too: a submit that failed after enqueuing them has no
+    // read-back that would wait for them
+    if (p->q_up) SR_CUDA_CHECK(cudaStreamSynchronize(p->q_up));
+    if (p->q_down) SR_CUDA_CHECK(cudaStreamSynchronize(p->q_down));
     return SR_OK;
 }
 
